@@ -1,0 +1,412 @@
+"""Pins of the FP64 oracle to facts other than itself: published generator
+outputs, hand-traced worked examples (tests/golden), closed forms, special
+cases that reduce to exhaustive search, an independent library route for the
+exact graph, and invariants of Algorithm 2.  No GPU."""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+from conftest import read_golden
+from paper_1602_06819_gb300.inputs import Mixture
+
+# --------------------------------------------------------------------------
+# generator
+# --------------------------------------------------------------------------
+
+
+def test_splitmix64_published_outputs(orc):
+    for ln in read_golden("splitmix64.txt"):
+        seed, j, out = (int(t) for t in ln.split())
+        assert orc.splitmix64_output(seed, j) == out
+
+
+def test_draw_closed_forms(orc):
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        key = int(rng.integers(0, 2**63)) * 2 + int(rng.integers(0, 2))
+        j = int(rng.integers(0, 10**6))
+        x = orc.splitmix64_output(key, j)
+        # n = 2^b: the draw is the top b bits of x
+        for b in (1, 7, 20, 31):
+            assert orc.draw(key, j, 1 << b) == x >> (64 - b)
+        # any n: 0 <= r < n and r = floor(x * n / 2^64) in exact integers
+        n = int(rng.integers(1, 5_000_000))
+        r = orc.draw(key, j, n)
+        assert 0 <= r < n and r == (x * n) >> 64
+
+
+def test_draws_are_roughly_uniform(orc):
+    key = orc.search_key(4, 17)
+    n = 10
+    counts = np.bincount([orc.draw(key, j, n) for j in range(20000)], minlength=n)
+    assert counts.min() > 1800 and counts.max() < 2200
+
+
+# --------------------------------------------------------------------------
+# exact graph (Sec. 2.1)
+# --------------------------------------------------------------------------
+
+
+def test_exact_graph_hand_example(orc):
+    X = np.array([[0.0], [1.0], [3.0], [6.0], [10.0]], np.float32)
+    ids, sims, margin = orc.exact_knn(X, 2)
+    for ln in read_golden("exact_line5.txt"):
+        t = [int(v) for v in ln.split()]
+        u, nb, dist = t[0], t[1:3], t[3:5]
+        assert list(ids[u]) == nb
+        np.testing.assert_allclose(sims[u], [1.0 / (1.0 + v) for v in dist], rtol=1e-15)
+
+
+def _exact_by_library(X, k):
+    """Independent route: scipy distance matrix + numpy lexsort."""
+    D = cdist(X.astype(np.float64), X.astype(np.float64))
+    n = X.shape[0]
+    out = np.empty((n, k), np.int64)
+    for u in range(n):
+        sims = 1.0 / (1.0 + D[u])
+        order = np.lexsort((np.arange(n), -sims))
+        order = order[order != u]
+        out[u] = order[:k]
+    return out
+
+
+@pytest.mark.parametrize("n,d,k,seed", [(60, 3, 5, 1), (200, 16, 10, 2), (150, 7, 1, 3),
+                                        (31, 128, 30, 4)])
+def test_exact_graph_matches_library_route(orc, n, d, k, seed):
+    X = np.random.default_rng(seed).standard_normal((n, d)).astype(np.float32)
+    ids, sims, _ = orc.exact_knn(X, k)
+    np.testing.assert_array_equal(ids, _exact_by_library(X, k))
+    # every list: k distinct non-self ids sorted best first, sims recomputed
+    for u in range(n):
+        assert len(set(ids[u])) == k and u not in ids[u]
+        assert np.all(np.diff(sims[u]) <= 0)
+        for v, s in zip(ids[u], sims[u]):
+            assert s == pytest.approx(1 / (1 + np.linalg.norm(X[u].astype(np.float64) - X[v])),
+                                      rel=1e-12)
+
+
+def test_exact_graph_duplicates_and_row_subset(orc):
+    X = np.random.default_rng(5).standard_normal((40, 4)).astype(np.float32)
+    X[7] = X[3]
+    X[20] = X[3]
+    ids, sims, margin = orc.exact_knn(X, 3)
+    assert list(ids[3][:2]) == [7, 20] and sims[3][0] == 1.0
+    assert list(ids[7][:2]) == [3, 20]
+    assert list(ids[20][:2]) == [3, 7]
+    rows = np.array([20, 3, 11])
+    ids2, sims2, _ = orc.exact_knn(X, 3, rows=rows)
+    np.testing.assert_array_equal(ids2, ids[rows])
+
+
+def test_exact_graph_skips_removed(orc):
+    X = np.random.default_rng(6).standard_normal((50, 5)).astype(np.float32)
+    removed = np.zeros(50, np.uint8)
+    removed[[4, 9, 33]] = 1
+    ids, _, _ = orc.exact_knn(X, 6, removed=removed)
+    full = _exact_by_library(np.delete(X, [4, 9, 33], axis=0), 6)
+    keep = np.array([i for i in range(50) if not removed[i]])
+    for row, u in enumerate(keep):
+        assert list(ids[u]) == list(keep[full[row]])
+
+
+# --------------------------------------------------------------------------
+# iGNNS (Sec. 3)
+# --------------------------------------------------------------------------
+
+
+def _line_graph_12():
+    X = np.arange(12, dtype=np.float32)[:, None]
+    nbr = np.array([[1, 2]] + [[i - 1, i + 1] for i in range(1, 11)] + [[10, 9]], np.int64)
+    return X, nbr
+
+
+def test_ignns_hand_traces(orc):
+    X, nbr = _line_graph_12()
+    q = np.array([8.2], np.float32)
+    for ln in read_golden("ignns_line12.txt"):
+        head, draws, result, counts = (p.split() for p in ln.split("|"))
+        e, speedup = float(head[1]), float(head[2])
+        r = orc.search(X, nbr, q, 3, speedup, e, seed=0, stream=0,
+                       draws=[int(v) for v in draws])
+        assert list(r.ids) == [int(v) for v in result], head[0]
+        ev, rs, dc, mv, du = (int(v) for v in counts)
+        assert (r.evals, r.restarts, r.discarded, r.moves, r.draws) == (ev, rs, dc, mv, du), head[0]
+        assert r.budget == math.floor(12 / speedup)
+
+
+def test_ignns_hand_trace_scan_order(orc):
+    for ln in read_golden("ignns_gaps10.txt"):
+        pts, head, draws, result, counts = (p.split() for p in ln.split("|"))
+        X = np.array([[float(v)] for v in pts], np.float32)
+        nbr, _, _ = orc.exact_knn(X, 3)
+        assert nbr.tolist() == [[1, 2, 3], [2, 0, 3], [3, 1, 4], [4, 2, 5], [5, 3, 6],
+                                [6, 4, 7], [7, 5, 8], [8, 6, 9], [9, 7, 6], [8, 7, 6]]
+        q, k_out, e, speedup = float(head[0]), int(head[1]), float(head[2]), float(head[3])
+        r = orc.search(X, nbr, np.array([q], np.float32), k_out, speedup, e, seed=0,
+                       stream=0, draws=[int(v) for v in draws])
+        assert list(r.ids) == [int(v) for v in result]
+        assert (r.evals, r.restarts, r.discarded, r.moves, r.draws) == tuple(int(v) for v in counts)
+
+
+def test_ignns_exhaustive_special_case(orc):
+    """speedup = 1 and no expansion test: every node is evaluated, so iGNNS is
+    linear search (Sec. 2.1) and returns the exact k nearest."""
+    mix = Mixture(d=8, components=5, half_width=5.0, sigma=1.0, seed=3)
+    X = mix.sample(300, 1)
+    nbr, _, _ = orc.exact_knn(X, 6)
+    Q = mix.sample(20, 2)
+    for i, q in enumerate(Q):
+        r = orc.search(X, nbr, q, 10, 1.0, math.inf, seed=9, stream=i)
+        sims = 1.0 / (1.0 + np.linalg.norm(X.astype(np.float64) - q.astype(np.float64), axis=1))
+        expect = np.lexsort((np.arange(300), -sims))[:10]
+        assert list(r.ids) == list(expect)
+        assert r.evals == 300 and r.discarded == 0
+        np.testing.assert_allclose(r.sims, sims[expect], rtol=1e-13)
+
+
+@pytest.mark.parametrize("speedup,e", [(2, 5.0), (4, 1.2), (7.5, 2.0), (16, math.inf), (50, 5.0)])
+def test_ignns_budget_is_exact(orc, speedup, e):
+    """The search computes exactly B = floor(n/speedup) similarities (Sec. 3)
+    whenever fewer than all live nodes fit in the budget."""
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=5)
+    X = mix.sample(1000, 1)
+    nbr, _, _ = orc.exact_knn(X, 10)
+    for i, q in enumerate(mix.sample(10, 2)):
+        r = orc.search(X, nbr, q, 10, speedup, e, seed=1, stream=i)
+        assert r.evals == r.budget == max(1, math.floor(1000 / speedup))
+        assert len(set(r.ids)) == 10
+        assert np.all(np.diff(r.sims) <= 0)
+        assert r.restarts >= 1 and r.discarded <= r.restarts
+
+
+def test_ignns_budget_floor_is_one(orc):
+    """A speedup above n still computes one similarity: B = max(1, floor(n/speedup))."""
+    X, nbr = _line_graph_12()
+    r = orc.search(X, nbr, np.array([8.2], np.float32), 3, 100.0, 2.0, seed=1, stream=2)
+    assert r.budget == 1 and r.evals == 1 and r.restarts == 1
+    assert r.ids[0] >= 0 and list(r.ids[1:]) == [-1, -1]
+
+
+def test_ignns_results_are_true_similarities_and_skip_removed(orc):
+    mix = Mixture(d=4, components=3, half_width=4.0, sigma=1.0, seed=8)
+    X = mix.sample(200, 1)
+    nbr, _, _ = orc.exact_knn(X, 5)
+    removed = np.zeros(200, np.uint8)
+    removed[::3] = 1
+    q = mix.sample(1, 2)[0]
+    r = orc.search(X, nbr, q, 8, 1.0, math.inf, seed=2, stream=5, removed=removed)
+    live = np.flatnonzero(removed == 0)
+    sims = 1.0 / (1.0 + np.linalg.norm(X[live].astype(np.float64) - q, axis=1))
+    expect = live[np.lexsort((live, -sims))[:8]]
+    assert list(r.ids) == list(expect)
+    assert r.evals == live.size
+
+
+def test_ignns_deterministic_per_stream(orc):
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=5)
+    X = mix.sample(500, 1)
+    nbr, _, _ = orc.exact_knn(X, 10)
+    q = mix.sample(1, 2)[0]
+    a = orc.search(X, nbr, q, 10, 4, 5.0, seed=1, stream=3)
+    b = orc.search(X, nbr, q, 10, 4, 5.0, seed=1, stream=3)
+    c = orc.search(X, nbr, q, 10, 4, 5.0, seed=1, stream=4)
+    assert list(a.ids) == list(b.ids) and a.evals == b.evals and a.draws == b.draws
+    assert a.draws != c.draws or list(a.ids) != list(c.ids) or a.moves != c.moves
+
+
+def test_rescore_orders_by_exact_similarity(orc):
+    X = np.random.default_rng(1).standard_normal((30, 6)).astype(np.float32)
+    q = X[0] + 0.01
+    cand = np.array([5, 0, 17, 3, -1, 22], np.int64)
+    ids, sims, _ = orc.rescore(X, q, cand, 3)
+    s = {int(c): 1 / (1 + np.linalg.norm(X[c].astype(np.float64) - q)) for c in cand if c >= 0}
+    expect = sorted(s, key=lambda c: (-s[c], c))[:3]
+    assert list(ids) == expect
+
+
+# --------------------------------------------------------------------------
+# Update (Algorithm 2)
+# --------------------------------------------------------------------------
+
+
+def test_update_hand_traces(orc):
+    X = np.array([[0], [1], [3], [6], [10], [15], [7]], np.float32)
+    for ln in read_golden("update_line6.txt"):
+        head, lists, counts = (p.split() for p in ln.split("|"))
+        depth = int(head[0])
+        ids, sims, _ = orc.exact_knn(X[:6], 2)
+        nbr_ids = np.full((7, 2), -1, np.int64)
+        nbr_sims = np.full((7, 2), -np.inf)
+        nbr_ids[:6], nbr_sims[:6] = ids, sims
+        L_ids, L_sims = np.array([3, 4]), np.array([0.5, 0.25])
+        nbr_ids[6], nbr_sims[6] = L_ids, L_sims
+        st = orc.update(X, 7, nbr_ids, nbr_sims, 6, L_ids, L_sims, depth)
+        assert nbr_ids.ravel().tolist() == [int(v) for v in lists], depth
+        assert (st.evals, st.literal_evals, st.offers_taken) == tuple(int(v) for v in counts)
+        # sims stored with the lists stay the true similarities
+        for u in range(7):
+            for v, s in zip(nbr_ids[u], nbr_sims[u]):
+                assert s == pytest.approx(1 / (1 + abs(float(X[u, 0]) - float(X[v, 0]))), rel=1e-15)
+
+
+@pytest.mark.parametrize("n,d,k,seed", [(80, 3, 4, 1), (300, 16, 10, 2), (120, 32, 7, 3)])
+def test_full_update_gives_exact_graph(orc, n, d, k, seed):
+    """Adding one point can only displace entries: an exact graph on n points,
+    the exact list of the new point, and an offer to every node give the exact
+    graph on n+1 points.  This checks the offer rule ("if needed, add new",
+    Algorithm 2) against brute force."""
+    mix = Mixture(d=d, components=4, half_width=6.0, sigma=1.0, seed=seed)
+    X = mix.sample(n + 1, seed + 10)
+    ids, sims, _ = orc.exact_knn(X[:n], k)
+    nbr_ids = np.vstack([ids, np.full((1, k), -1)]).astype(np.int64)
+    nbr_sims = np.vstack([sims, np.full((1, k), -np.inf)])
+    L_ids, L_sims, _ = orc.exact_knn(X, k, rows=[n])
+    nbr_ids[n], nbr_sims[n] = L_ids[0], L_sims[0]
+    orc.update(X, n + 1, nbr_ids, nbr_sims, n, L_ids[0], L_sims[0], 2, full=True)
+    exact_ids, exact_sims, _ = orc.exact_knn(X, k)
+    np.testing.assert_array_equal(nbr_ids, exact_ids)
+    np.testing.assert_allclose(nbr_sims, exact_sims, rtol=1e-15)
+
+
+def test_update_invariants(orc):
+    """Update never lowers a list's k-th similarity, keeps lists sorted with k
+    distinct non-self ids, and computes at most k^2 new similarities at DEPTH 2
+    (k + k^2 counting the level-1 nodes as Algorithm 2 does)."""
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=7)
+    X = mix.sample(600, 1)
+    k = 10
+    g = orc.Graph.exact(X[:500], k, capacity=600)
+    g.X[500:] = X[500:]
+    for new in range(500, 600):
+        before = g.sims[:new, k - 1].copy()
+        L = g.search(X[new], k, 4, 5.0, 1, new)
+        g.ids[new], g.sims[new] = L.ids, L.sims
+        st = orc.update(g.X, new + 1, g.ids, g.sims, new, L.ids, L.sims, 2)
+        g.n = new + 1
+        assert np.all(g.sims[:new, k - 1] >= before)
+        assert st.evals <= k * k and st.literal_evals <= k + k * k
+    for u in range(600):
+        assert len(set(g.ids[u])) == k and u not in g.ids[u]
+        assert np.all(np.diff(g.sims[u]) <= 0)
+
+
+# --------------------------------------------------------------------------
+# sequential online build (Algorithm 1)
+# --------------------------------------------------------------------------
+
+
+def test_insert_stream_matches_explicit_steps(orc):
+    """Algorithm 1 is iGNNS then Update for each point in turn."""
+    mix = Mixture(d=8, components=4, half_width=6.0, sigma=1.0, seed=2)
+    X = mix.sample(260, 1)
+    a = orc.Graph.exact(X[:200], 6, capacity=260)
+    st = a.insert_stream(X[200:], 3, 5.0, 2, seed=11)
+    b = orc.Graph.exact(X[:200], 6, capacity=260)
+    b.X[200:] = X[200:]
+    for new in range(200, 260):
+        L = orc.search(b.X, b.ids[:new], X[new], 6, 3, 5.0, 11, new, n=new)
+        b.ids[new], b.sims[new] = L.ids, L.sims
+        u = orc.update(b.X, new + 1, b.ids, b.sims, new, L.ids, L.sims, 2)
+        assert st["search_evals"][new - 200] == L.evals
+        assert st["update_evals"][new - 200] == u.evals
+    np.testing.assert_array_equal(a.ids, b.ids)
+
+
+def test_exhaustive_insert_gives_exact_new_list(orc):
+    mix = Mixture(d=8, components=4, half_width=6.0, sigma=1.0, seed=4)
+    X = mix.sample(151, 1)
+    g = orc.Graph.exact(X[:150], 5, capacity=151)
+    g.insert_stream(X[150:], 1.0, math.inf, 2, seed=3)
+    exact, _, _ = orc.exact_knn(X, 5, rows=[150])
+    assert list(g.ids[150]) == list(exact[0])
+
+
+def test_depth_sweep_recall_grows_then_flattens(orc):
+    """Sec. 8.3: deeper updates give better graphs with diminishing returns."""
+    mix = Mixture(d=3, components=10, half_width=10.0, sigma=1.0, seed=9)
+    X = mix.sample(800, 1)
+    exact, _, _ = orc.exact_knn(X, 10)
+    rec = {}
+    for depth in (1, 2, 3):
+        g = orc.Graph.exact(X[:400], 10, capacity=800)
+        g.insert_stream(X[400:], 4, 5.0, depth, seed=5)
+        rec[depth] = orc.correct_edges(g.ids, exact) / exact.size
+    assert rec[1] < rec[2] <= rec[3] + 0.005
+    assert rec[3] - rec[2] < rec[2] - rec[1]
+
+
+# --------------------------------------------------------------------------
+# graph quality (Sec. 8.5)
+# --------------------------------------------------------------------------
+
+
+def test_quality_q_hand_values(orc):
+    for ln in read_golden("quality_q.txt"):
+        n, n_a, k, e_c, q = ln.split()
+        assert orc.quality_q(int(e_c), int(n), int(n_a), int(k)) == pytest.approx(float(q),
+                                                                                   rel=1e-9)
+
+
+def test_correct_edges_counts_directed_overlap(orc):
+    a = np.array([[1, 2], [0, 2], [0, 1]])
+    b = np.array([[2, 1], [2, 0], [1, 3]])
+    assert orc.correct_edges(a, b) == 5
+    assert orc.correct_edges(a, a) == 6
+
+
+# --------------------------------------------------------------------------
+# screening storage codes
+# --------------------------------------------------------------------------
+
+
+def test_bf16_codes_match_torch(orc):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.standard_normal(20000) * 30, rng.standard_normal(1000) * 1e-30,
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, 65504.0, 3.4e38]]).astype(np.float32)
+    codes, deq = orc.quantize_bf16(x)
+    t = torch.from_numpy(x).to(torch.bfloat16)
+    np.testing.assert_array_equal(codes, t.view(torch.int16).numpy().view(np.uint16))
+    np.testing.assert_array_equal(deq, t.float().numpy())
+
+
+def test_e4m3_codes_hand_values(orc):
+    for v, c in [(0.0, 0x00), (1.0, 0x38), (-1.75, 0xBE), (448.0, 0x7E), (500.0, 0x7E),
+                 (-1e9, 0xFE), (2.0**-9, 0x01), (2.0**-6, 0x08), (2.0**-10, 0x00),
+                 (3 * 2.0**-11, 0x01), (1.0625, 0x38), (1.1875, 0x3A),
+                 (0.0625 * 1.0625, 0x18), (464.0 - 1e-3, 0x7E)]:
+        assert orc.e4m3_code(v) == c, v
+    for c in range(256):
+        if c & 0x7F == 0x7F:
+            continue                       # the two NaN codes
+        assert orc.e4m3_code(orc.e4m3_value(c)) == c
+
+
+def test_e4m3_codes_match_torch_in_range(orc):
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8")
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.uniform(-448, 448, 20000), rng.standard_normal(20000),
+                        rng.standard_normal(5000) * 1e-3]).astype(np.float32)
+    codes = np.array([orc.e4m3_code(float(v)) for v in x], np.uint8)
+    t = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    np.testing.assert_array_equal(codes, t)
+
+
+def test_e4m3_rowwise_scale(orc):
+    X = np.random.default_rng(7).standard_normal((50, 96)).astype(np.float32) * 20
+    X[3] = 0
+    codes, scales, deq = orc.quantize_e4m3(X)
+    amax = np.abs(X).max(1)
+    np.testing.assert_array_equal(scales[amax > 0], (amax[amax > 0] / np.float32(448)).astype(np.float32))
+    assert scales[3] == 1.0 and np.all(deq[3] == 0)
+    # the largest element of every row maps to +-448 exactly
+    for r in range(50):
+        if amax[r] > 0:
+            assert np.abs(deq[r]).max() == pytest.approx(amax[r], rel=2e-7)
+    # relative error of E4M3 is at most 2^-4 of the value (3 mantissa bits)
+    big = np.abs(X) > scales[:, None] * 2.0**-6
+    assert np.all(np.abs(deq - X)[big] <= np.abs(X)[big] * 2.0**-4 * 1.0001)
