@@ -1,0 +1,189 @@
+/*
+ * knn_graph.h -- C ABI of the online k-nn graph library for one GB300
+ * (sm_103a).
+ *
+ * The method is the online approximate k-nn graph of Debatty, Michiardi and
+ * Mees, "Fast Online k-nn Graph Building" (KDD'16): each new point is placed
+ * by an iGNNS graph search (Sec. 3) followed by the reverse Update walk
+ * (Algorithm 2), as in the sequential build of Algorithm 1.  The initial graph
+ * and the ground truth come from a brute-force exact k-nn graph (Sec. 2.1).
+ *
+ * Conventions shared by every call:
+ *   - Similarity is sim(a, b) = 1 / (1 + ||a - b||_2) (the Euclidean distance
+ *     of the paper's synthetic data, Sec. 8.1); higher is closer.  Every
+ *     neighbour list is sorted best first; equal similarities go to the lower
+ *     id.
+ *   - Ids are dense insertion indices: the initial points are 0 .. n_init-1,
+ *     the i-th inserted point gets the next free id.
+ *   - Vectors are row-major float32 [m, dim].  Outputs are row-major.
+ *   - Every pointer argument may be host memory (pageable or pinned) or
+ *     device memory of the graph's device; the library tells them apart with
+ *     cudaPointerGetAttributes and stages host buffers itself.  Pinned host
+ *     memory gives asynchronous copies.  The caller owns every buffer it
+ *     passes; the library owns the graph.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     ordered on it; device outputs are valid once the stream has reached the
+ *     call, host outputs when the call returns (calls that write host memory
+ *     synchronise the stream).
+ *   - No call aborts.  Each returns a knn_status; on error, knn_last_error()
+ *     gives a message for the calling thread.  A graph handle is not
+ *     thread-safe: one thread (or external locking) per handle.
+ */
+#ifndef KNN_GRAPH_H
+#define KNN_GRAPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define KNN_API __attribute__((visibility("default")))
+#else
+#define KNN_API
+#endif
+
+typedef enum knn_status {
+    KNN_OK = 0,
+    KNN_ERR_INVALID_ARG = -1,    /* a bad size, pointer or parameter           */
+    KNN_ERR_OOM = -2,            /* device memory admission refused            */
+    KNN_ERR_CAPACITY = -3,       /* the graph or a batch would exceed its size */
+    KNN_ERR_CUDA = -4,           /* a CUDA runtime call failed                 */
+    KNN_ERR_DEVICE_TIMEOUT = -5, /* a bounded device wait gave up              */
+    KNN_ERR_NOT_FOUND = -6,      /* an id that is not in the graph             */
+    KNN_ERR_UNSUPPORTED = -7     /* a size outside the compiled kernels        */
+} knn_status;
+
+typedef enum knn_storage {
+    KNN_STORAGE_FP32 = 0,     /* searched in FP32                               */
+    KNN_STORAGE_BF16 = 1,     /* screened in BF16, best candidates re-scored    */
+    KNN_STORAGE_FP8_E4M3 = 2  /* screened in FP8-E4M3 with a per-row scale      */
+} knn_storage;
+
+/* Parameters of a graph.  The names follow the paper. */
+typedef struct knn_params {
+    int32_t dim;          /* vector dimension d, 1 .. 256                         */
+    int32_t k;            /* neighbours per node, 1 .. 32 (Sec. 1)                */
+    int32_t depth;        /* Update DEPTH (Algorithm 2), 1 or 2                   */
+    int32_t storage;      /* knn_storage of the searched copy                     */
+    double speedup;       /* iGNNS budget: B = max(1, floor(n / speedup))
+                             similarities per search (Sec. 3); > 0                */
+    double expansion;     /* e > 1: a restart r is discarded when
+                             sim(q, r) < s_max / e (Sec. 3); <= 0 or +inf
+                             disables the test                                   */
+    int32_t rescore_mult; /* screening forms: keep rescore_mult * k candidates
+                             and re-score them in FP32; ignored for FP32         */
+    int32_t max_batch;    /* largest m of one insert or query call, >= 1        */
+    uint64_t seed;        /* seed of every restart draw                          */
+    int64_t capacity;     /* most nodes the graph will ever hold                 */
+} knn_params;
+
+/* Running totals of a graph (Sec. 8.3 counts similarity computations). */
+typedef struct knn_stats {
+    int64_t n;               /* nodes in the graph                                 */
+    int64_t capacity;
+    int64_t removed;         /* nodes removed                                      */
+    int64_t inserts;         /* points inserted after creation                     */
+    int64_t queries;         /* queries answered                                   */
+    int64_t search_evals;    /* similarities computed by iGNNS searches            */
+    int64_t update_evals;    /* similarities computed by Update beyond level 1     */
+    int64_t cross_evals;     /* similarities among the points of one insert batch  */
+    int64_t rescore_evals;   /* FP32 re-scores of screening candidates             */
+    int64_t restarts;        /* random restart nodes evaluated                     */
+    int64_t moves;           /* eager hill-climbing moves                          */
+    int64_t adjacency_reads; /* neighbour lists scanned by the climbs              */
+    int64_t offers;          /* candidate (node, new) pairs merged by Update        */
+    int64_t device_bytes;    /* device memory held by the graph                    */
+} knn_stats;
+
+typedef struct knn_graph knn_graph; /* opaque, owned by the library */
+
+/*
+ * Create a graph from n_init >= k+1 points and build their exact k-nn graph
+ * by brute force (Sec. 2.1; the initial graph of Sec. 8.5 is built the same
+ * way).  init_vecs: [n_init, dim] float32.  Allocates all device memory the
+ * graph will need for `capacity` nodes and `max_batch`-sized calls; returns
+ * KNN_ERR_OOM if the device lacks it.  *out receives the handle.
+ */
+KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_vecs,
+                                    int64_t n_init, void *stream, knn_graph **out);
+
+/*
+ * Insert m points (1 <= m <= max_batch), Algorithm 1 for a batch: every point
+ * is searched with iGNNS against the graph as it stood before the call, using
+ * the restart stream equal to its new id; the exact similarities among the m
+ * points are merged into their lists (the batch analogue of each point seeing
+ * the ones before it); then Update (Algorithm 2) offers each new point to
+ * its neighbours and their neighbours up to DEPTH.  vecs: [m, dim] float32.
+ * out_ids (nullable): [m] int64 ids given to the points.
+ * out_nbrs (nullable): [m, k] int64, the neighbour list each new point got.
+ * KNN_ERR_CAPACITY if n + m > capacity.
+ */
+KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64_t m,
+                                          int64_t *out_ids, int64_t *out_nbrs, void *stream);
+
+/*
+ * Answer m queries (1 <= m <= max_batch) with iGNNS (Sec. 3) against the
+ * current graph, without changing it.  Query i uses restart stream
+ * 2^63 + query_id0 + i, so a request's result depends only on the graph, the
+ * seed and its id, not on the batch it travels in.  vecs: [m, dim] float32.
+ * out_ids: [m, k_out] int64 (-1 where fewer were found); out_sims (nullable):
+ * [m, k_out] float32 similarities.  1 <= k_out <= k.
+ */
+KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_t m,
+                                         int32_t k_out, uint64_t query_id0,
+                                         int64_t *out_ids, float *out_sims, void *stream);
+
+/*
+ * Remove m nodes (not in the paper).  Removed nodes are never drawn, climbed
+ * to, returned or offered again; lists that still hold them keep the entry.
+ * KNN_ERR_NOT_FOUND if an id is outside 0 .. n-1.  ids: [m] int64.
+ */
+KNN_API knn_status knn_graph_remove(knn_graph *g, const int64_t *ids, int64_t m,
+                                    void *stream);
+
+/*
+ * Copy out the adjacency lists of nodes 0 .. min(n, n_cap)-1.
+ * out_ids: [n_cap, k] int64 (-1 for an empty slot); out_sims (nullable):
+ * [n_cap, k] float32.  *n_out (host) receives the number of rows written.
+ */
+KNN_API knn_status knn_graph_get_edges(knn_graph *g, int64_t *out_ids, float *out_sims,
+                                       int64_t n_cap, int64_t *n_out, void *stream);
+
+/*
+ * Per-item counters of the last insert or query call: for each of its m
+ * items, 8 int64 values: search similarities (iGNNS budget spent), Update
+ * similarities (levels >= 2), restarts evaluated, restarts discarded by the
+ * expansion test, eager moves, neighbour lists scanned, restart draws made
+ * (free redraws included), and 0.  out: [m, 8] int64; m <= the last call's m.
+ */
+KNN_API knn_status knn_graph_last_counters(knn_graph *g, int64_t *out, int64_t m,
+                                           void *stream);
+
+/* Running totals (synchronises the graph's last stream). */
+KNN_API knn_status knn_graph_stats(knn_graph *g, knn_stats *out);
+
+/* Release the graph and all its device memory.  NULL is a no-op. */
+KNN_API void knn_graph_destroy(knn_graph *g);
+
+/*
+ * Brute-force exact k-nn graph of n points (Sec. 2.1: every pairwise
+ * similarity, keep the k best per node, ties to the lower id), without a
+ * graph handle: the initial graph and the ground truth of Sec. 8.5.
+ * X: [n, dim] float32, n >= k+1, 1 <= k <= 32.  out_ids: [n, k] int64;
+ * out_sims (nullable): [n, k] float32.  Allocates its own temporaries.
+ */
+KNN_API knn_status knn_exact_graph(const float *X, int64_t n, int32_t dim, int32_t k,
+                                   int64_t *out_ids, float *out_sims, void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+KNN_API const char *knn_last_error(void);
+
+/* Library version string. */
+KNN_API const char *knn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KNN_GRAPH_H */

@@ -1,0 +1,641 @@
+// graph.cu -- the C ABI of include/knn_graph.h: graph lifecycle, host/device
+// staging, and the kernel pipeline of one insert or query batch.
+//
+// Device layout of a graph with capacity C, padded dimension DP, k neighbours
+// and batches of at most M points:
+//   X        [C][DP]  float32 rows (the exact copy; zero padded)
+//   Xb / X8  [C][DP]  BF16 / FP8-E4M3 screening copy, scale [C] for FP8
+//   nbr_ids  [C][k]   int32 adjacency, best first, -1 = empty slot
+//   nbr_d2   [C][k]   float32 squared distances of those entries
+//   removed  [C/32]   bitset of removed nodes
+//   head     [C]      chain heads of Update candidates (-1 = none)
+//   visited  [M][C/32] per-query visited bitsets, cleared per batch
+//   plus per-batch keys, counters and the Update candidate pool
+//   (M * (k + k^2) entries).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "knn_graph.h"
+#include "kernels.h"
+
+using namespace knn;
+
+struct knn_graph {
+    knn_params p;
+    int device = 0;
+    int sm_count = 0;
+    int dp = 0;
+    int KT = 0;            // candidates kept by an insert's search
+    int hash_size = 0;
+    int64_t n = 0;
+    int64_t n_removed = 0;
+    int64_t inserts = 0, queries = 0;
+    int64_t last_m = 0;
+    int64_t vwords = 0;
+    unsigned offer_cap = 0;
+    size_t bytes = 0;
+    std::vector<void *> allocations;
+    std::vector<uint32_t> removed_host;
+
+    float *X = nullptr;
+    uint16_t *Xb = nullptr;
+    uint8_t *X8 = nullptr;
+    float *scale = nullptr;
+    int32_t *nbr_ids = nullptr;
+    float *nbr_d2 = nullptr;
+    uint32_t *removed = nullptr;
+    int32_t *head = nullptr;
+    uint32_t *visited = nullptr;
+    float *qbuf = nullptr;
+    float *stage_in = nullptr;
+    uint64_t *keys_search = nullptr;
+    uint64_t *keys_final = nullptr;
+    long long *counters = nullptr;
+    uint64_t *offer_key = nullptr;
+    int32_t *offer_next = nullptr;
+    int32_t *touched = nullptr;
+    unsigned *small = nullptr;  // [0] offers, [1] touched, [2] error flags
+    unsigned long long *totals = nullptr;
+    int64_t *out_ids_dev = nullptr;
+    float *out_sims_dev = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static knn_status fail(knn_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CU(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(KNN_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                 \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+static int64_t budget_of(int64_t n, double speedup) {
+    // B = max(1, floor(n / speedup)), the iGNNS similarity budget (Sec. 3)
+    double b = std::floor((double)n / speedup);
+    return b < 1.0 ? 1 : (int64_t)b;
+}
+
+static int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <class T>
+static knn_status dev_alloc(knn_graph *g, T **ptr, size_t count) {
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KNN_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    g->allocations.push_back(p);
+    g->bytes += bytes;
+    *ptr = static_cast<T *>(p);
+    return KNN_OK;
+}
+
+static void free_graph(knn_graph *g) {
+    for (void *p : g->allocations) cudaFree(p);
+    delete g;
+}
+
+#define TRY(expr)                               \
+    do {                                        \
+        knn_status st_ = (expr);                \
+        if (st_ != KNN_OK) return st_;          \
+    } while (0)
+
+// Copy m rows of `dim` floats (host or device) into the rows starting at
+// row `first` of the graph's arrays, with the screening copy if any.
+static knn_status append_rows(knn_graph *g, const float *vecs, int64_t m, int64_t first,
+                              float *dst_rows, bool screening, cudaStream_t s) {
+    const int d = g->p.dim, dp = g->dp;
+    const bool dev = is_device_ptr(vecs);
+    for (int64_t c0 = 0; c0 < m; c0 += g->p.max_batch) {
+        const int64_t cm = std::min<int64_t>(g->p.max_batch, m - c0);
+        const float *src = vecs + c0 * d;
+        if (!dev) {
+            CU(cudaMemcpyAsync(g->stage_in, src, (size_t)cm * d * sizeof(float), cudaMemcpyHostToDevice, s));
+            src = g->stage_in;
+        }
+        const int64_t r = first + c0;
+        CU(launch_append(src, cm, d, dp, dst_rows + r * dp,
+                         (screening && g->Xb) ? g->Xb + r * dp : nullptr,
+                         (screening && g->X8) ? g->X8 + r * dp : nullptr,
+                         (screening && g->X8) ? g->scale + r : nullptr, s));
+    }
+    return KNN_OK;
+}
+
+static const uint8_t *searched_rows(const knn_graph *g) {
+    switch (g->p.storage) {
+        case KNN_STORAGE_BF16: return reinterpret_cast<const uint8_t *>(g->Xb);
+        case KNN_STORAGE_FP8_E4M3: return g->X8;
+        default: return reinterpret_cast<const uint8_t *>(g->X);
+    }
+}
+
+// iGNNS for m items whose padded FP32 query rows start at `queries`; leaves
+// the best k_out keys of each item in g->keys_final (screening forms) or
+// g->keys_search (FP32), and returns which.
+static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int k_out,
+                             uint64_t stream_base, cudaStream_t s, const uint64_t **keys_out) {
+    const bool screening = g->p.storage != KNN_STORAGE_FP32;
+    const int KT = screening ? g->p.rescore_mult * k_out : k_out;
+    CU(cudaMemsetAsync(g->visited, 0, (size_t)m * g->vwords * sizeof(uint32_t), s));
+    SearchArgs a{};
+    a.rows = searched_rows(g);
+    a.row_scale = g->scale;
+    a.nbr = g->nbr_ids;
+    a.removed = g->removed;
+    a.queries = queries;
+    a.q_stride = g->dp;
+    a.visited = g->visited;
+    a.vwords = g->vwords;
+    a.out_keys = g->keys_search;
+    a.counters = g->counters;
+    a.totals = g->totals;
+    a.m = (int32_t)m;
+    a.k = g->p.k;
+    a.KT = KT;
+    a.n = (uint32_t)g->n;
+    a.n_live = g->n - g->n_removed;
+    a.budget = budget_of(g->n, g->p.speedup);
+    a.max_draws = 64ull * (uint64_t)g->n;
+    a.seed = g->p.seed;
+    a.stream_base = stream_base;
+    const double e = g->p.expansion;
+    a.discard = (e > 0.0 && std::isfinite(e)) ? 1 : 0;
+    a.expansion = a.discard ? (float)e : 1.0f;
+    CU(launch_search(g->p.storage, g->dp, a, s));
+    if (!screening) {
+        *keys_out = g->keys_search;
+        return KNN_OK;
+    }
+    RescoreArgs r{};
+    r.rows = g->X;
+    r.queries = queries;
+    r.q_stride = g->dp;
+    r.cand_keys = g->keys_search;
+    r.out_keys = g->keys_final;
+    r.totals = g->totals;
+    r.m = (int32_t)m;
+    r.KT = KT;
+    r.k_out = k_out;
+    CU(launch_rescore(g->dp, r, s));
+    *keys_out = g->keys_final;
+    return KNN_OK;
+}
+
+// Write m*k int64 ids (and optional sims) from keys to a host or device buffer.
+static knn_status emit_keys(knn_graph *g, const uint64_t *keys, int64_t m, int kk, int k_out,
+                            int64_t *out_ids, float *out_sims, cudaStream_t s, bool *synced) {
+    const bool ids_dev = is_device_ptr(out_ids);
+    const bool sims_dev = out_sims == nullptr || is_device_ptr(out_sims);
+    int64_t *ids_target = ids_dev ? out_ids : g->out_ids_dev;
+    float *sims_target = out_sims ? (sims_dev ? out_sims : g->out_sims_dev) : nullptr;
+    CU(launch_keys_to_output(keys, m, kk, k_out, ids_target, sims_target, s));
+    bool need_sync = false;
+    if (!ids_dev) {
+        CU(cudaMemcpyAsync(out_ids, g->out_ids_dev, (size_t)m * k_out * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        need_sync = true;
+    }
+    if (out_sims && !sims_dev) {
+        CU(cudaMemcpyAsync(out_sims, g->out_sims_dev, (size_t)m * k_out * sizeof(float), cudaMemcpyDeviceToHost, s));
+        need_sync = true;
+    }
+    if (need_sync) {
+        CU(cudaStreamSynchronize(s));
+        *synced = true;
+    }
+    return KNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+KNN_API const char *knn_last_error(void) { return g_last_error.c_str(); }
+
+KNN_API const char *knn_version(void) { return "knn_graph 0.1 (sm_103a)"; }
+
+KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_vecs, int64_t n_init,
+                                    void *stream, knn_graph **out) {
+    if (!params || !init_vecs || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    const knn_params &p = *params;
+    if (p.dim < 1 || p.dim > 256) return fail(KNN_ERR_UNSUPPORTED, "dim %d outside 1..256", p.dim);
+    if (p.k < 1 || p.k > 32) return fail(KNN_ERR_UNSUPPORTED, "k %d outside 1..32", p.k);
+    if (p.depth < 1 || p.depth > 2) return fail(KNN_ERR_UNSUPPORTED, "depth %d outside 1..2", p.depth);
+    if (p.storage < 0 || p.storage > 2) return fail(KNN_ERR_INVALID_ARG, "bad storage %d", p.storage);
+    if (!(p.speedup > 0.0) || !std::isfinite(p.speedup))
+        return fail(KNN_ERR_INVALID_ARG, "speedup must be finite and > 0");
+    if (std::isnan(p.expansion)) return fail(KNN_ERR_INVALID_ARG, "expansion is NaN");
+    if (p.storage != KNN_STORAGE_FP32 && (p.rescore_mult < 1 || p.rescore_mult * p.k > 128))
+        return fail(KNN_ERR_UNSUPPORTED, "rescore_mult * k must be in 1..128");
+    if (p.max_batch < 1) return fail(KNN_ERR_INVALID_ARG, "max_batch must be >= 1");
+    if (n_init < p.k + 1) return fail(KNN_ERR_INVALID_ARG, "n_init %lld < k + 1", (long long)n_init);
+    if (p.capacity < n_init || p.capacity >= (int64_t)INT32_MAX)
+        return fail(KNN_ERR_CAPACITY, "capacity %lld must be >= n_init and < 2^31", (long long)p.capacity);
+
+    knn_graph *g = new knn_graph();
+    g->p = p;
+    if (g->p.storage == KNN_STORAGE_FP32) g->p.rescore_mult = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+        delete g;
+        cudaGetLastError();
+        return fail(KNN_ERR_CUDA, "no CUDA device");
+    }
+    g->dp = padded_dim(p.dim);
+    g->KT = g->p.rescore_mult * p.k;
+    g->hash_size = next_pow2(2 * (1 + p.k + p.k * p.k));
+    g->vwords = (p.capacity + 31) / 32;
+    const int64_t C = p.capacity, M = p.max_batch, K = p.k, DP = g->dp;
+    g->offer_cap = (unsigned)(M * (K + K * K));
+
+    // admission: everything the graph will ever need, allocated up front
+    size_t need = (size_t)C * DP * 4 + (size_t)C * K * 8 + (size_t)g->vwords * 4 + (size_t)C * 4 +
+                  (size_t)M * g->vwords * 4 + (size_t)M * DP * 4 + (size_t)M * p.dim * 4 +
+                  (size_t)M * g->KT * 8 + (size_t)M * K * 8 + (size_t)M * NCTR * 8 +
+                  (size_t)g->offer_cap * 16 + (size_t)M * K * 12;
+    if (p.storage == KNN_STORAGE_BF16) need += (size_t)C * DP * 2;
+    if (p.storage == KNN_STORAGE_FP8_E4M3) need += (size_t)C * DP + (size_t)C * 4;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete g;
+        cudaGetLastError();
+        return fail(KNN_ERR_CUDA, "cudaMemGetInfo failed");
+    }
+    if (need + (size_t)256 * 1024 * 1024 > free_b) {
+        delete g;
+        return fail(KNN_ERR_OOM, "graph needs %zu bytes, %zu free", need, free_b);
+    }
+
+    knn_status st = KNN_OK;
+#define ALLOC(ptr, count)                          \
+    if (st == KNN_OK) st = dev_alloc(g, &g->ptr, (size_t)(count));
+    ALLOC(X, C * DP)
+    if (p.storage == KNN_STORAGE_BF16) { ALLOC(Xb, C * DP) }
+    if (p.storage == KNN_STORAGE_FP8_E4M3) { ALLOC(X8, C * DP) ALLOC(scale, C) }
+    ALLOC(nbr_ids, C * K)
+    ALLOC(nbr_d2, C * K)
+    ALLOC(removed, g->vwords)
+    ALLOC(head, C)
+    ALLOC(visited, M * g->vwords)
+    ALLOC(qbuf, M * DP)
+    ALLOC(stage_in, M * p.dim)
+    ALLOC(keys_search, M * g->KT)
+    ALLOC(keys_final, M * K)
+    ALLOC(counters, M * NCTR)
+    ALLOC(offer_key, g->offer_cap)
+    ALLOC(offer_next, g->offer_cap)
+    ALLOC(touched, g->offer_cap)
+    ALLOC(small, 4)
+    ALLOC(totals, NTOT)
+    ALLOC(out_ids_dev, M * K)
+    ALLOC(out_sims_dev, M * K)
+#undef ALLOC
+    if (st != KNN_OK) {
+        free_graph(g);
+        return st;
+    }
+    g->removed_host.assign((size_t)g->vwords, 0u);
+
+    auto setup = [&]() -> knn_status {
+        CU(cudaMemsetAsync(g->X, 0, (size_t)C * DP * 4, s));
+        CU(cudaMemsetAsync(g->removed, 0, (size_t)g->vwords * 4, s));
+        CU(cudaMemsetAsync(g->small, 0, 16, s));
+        CU(cudaMemsetAsync(g->totals, 0, NTOT * 8, s));
+        CU(cudaMemsetAsync(g->counters, 0, (size_t)M * NCTR * 8, s));
+        CU(launch_fill_i32(g->head, -1, C, s));
+        CU(launch_fill_i32(g->nbr_ids, -1, C * K, s));
+        TRY(append_rows(g, init_vecs, n_init, 0, g->X, true, s));
+        ExactArgs ea{};
+        ea.X = g->X;
+        ea.removed = nullptr;
+        ea.out_ids = g->nbr_ids;
+        ea.out_d2 = g->nbr_d2;
+        ea.n = n_init;
+        ea.k = (int32_t)K;
+        CU(launch_exact(g->dp, ea, s));
+        CU(cudaStreamSynchronize(s));
+        return KNN_OK;
+    };
+    st = setup();
+    if (st != KNN_OK) {
+        free_graph(g);
+        return st;
+    }
+    g->n = n_init;
+    g->last_stream = s;
+    *out = g;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64_t m, int64_t *out_ids,
+                                          int64_t *out_nbrs, void *stream) {
+    if (!g || !vecs) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (m < 1 || m > g->p.max_batch)
+        return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
+    if (g->n + m > g->p.capacity) return fail(KNN_ERR_CAPACITY, "graph full");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    const int64_t n0 = g->n;
+    const int K = g->p.k;
+
+    // a1: store the new rows (and their screening copy)
+    TRY(append_rows(g, vecs, m, n0, g->X, true, s));
+    // a2-a5: iGNNS of every new point against the n0 nodes before the batch
+    const uint64_t *keys = nullptr;
+    TRY(run_search(g, g->X + n0 * g->dp, m, K, (uint64_t)n0, s, &keys));
+    // a6: exact similarities among the batch, written as the new lists
+    CrossArgs ca{};
+    ca.rows = g->X;
+    ca.in_keys = keys;
+    ca.nbr_ids = g->nbr_ids;
+    ca.nbr_d2 = g->nbr_d2;
+    ca.totals = g->totals;
+    ca.m = (int32_t)m;
+    ca.k = K;
+    ca.n = (uint32_t)n0;
+    CU(launch_cross(g->dp, ca, s));
+    // a7-a8: Update (Algorithm 2): collect candidates, then merge them
+    CU(cudaMemsetAsync(g->small, 0, 2 * sizeof(unsigned), s));
+    UpdateArgs ua{};
+    ua.rows = g->X;
+    ua.nbr_ids = g->nbr_ids;
+    ua.nbr_d2 = g->nbr_d2;
+    ua.removed = g->removed;
+    ua.head = g->head;
+    ua.offer_key = g->offer_key;
+    ua.offer_next = g->offer_next;
+    ua.touched = g->touched;
+    ua.offer_count = g->small + 0;
+    ua.touched_count = g->small + 1;
+    ua.offer_cap = g->offer_cap;
+    ua.error_flags = g->small + 2;
+    ua.counters = g->counters;
+    ua.totals = g->totals;
+    ua.m = (int32_t)m;
+    ua.k = K;
+    ua.depth = g->p.depth;
+    ua.hash_size = g->hash_size;
+    ua.n = (uint32_t)n0;
+    CU(launch_update(g->dp, ua, s));
+    MergeArgs ma{};
+    ma.nbr_ids = g->nbr_ids;
+    ma.nbr_d2 = g->nbr_d2;
+    ma.head = g->head;
+    ma.offer_key = g->offer_key;
+    ma.offer_next = g->offer_next;
+    ma.touched = g->touched;
+    ma.touched_count = g->small + 1;
+    ma.offer_count = g->small + 0;
+    ma.totals = g->totals;
+    ma.k = K;
+    CU(launch_merge(ma, g->sm_count, s));
+    // a9: publish
+    g->n = n0 + m;
+    g->inserts += m;
+    g->last_m = m;
+
+    if (out_ids) {
+        if (is_device_ptr(out_ids)) {
+            CU(launch_fill_ids(out_ids, n0, m, s));
+        } else {
+            for (int64_t i = 0; i < m; ++i) out_ids[i] = n0 + i;
+        }
+    }
+    if (out_nbrs) {
+        const bool dev = is_device_ptr(out_nbrs);
+        int64_t *target = dev ? out_nbrs : g->out_ids_dev;
+        CU(launch_lists_to_output(g->nbr_ids + n0 * K, g->nbr_d2 + n0 * K, m, K, target, nullptr, s));
+        if (!dev) {
+            CU(cudaMemcpyAsync(out_nbrs, g->out_ids_dev, (size_t)m * K * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+        }
+    }
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                         uint64_t query_id0, int64_t *out_ids, float *out_sims,
+                                         void *stream) {
+    if (!g || !vecs || !out_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (m < 1 || m > g->p.max_batch)
+        return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
+    if (k_out < 1 || k_out > g->p.k) return fail(KNN_ERR_INVALID_ARG, "k_out outside 1..k");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    TRY(append_rows(g, vecs, m, 0, g->qbuf, false, s));
+    const uint64_t *keys = nullptr;
+    TRY(run_search(g, g->qbuf, m, k_out, (1ull << 63) + query_id0, s, &keys));
+    bool synced = false;
+    TRY(emit_keys(g, keys, m, k_out, k_out, out_ids, out_sims, s, &synced));
+    g->queries += m;
+    g->last_m = m;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_remove(knn_graph *g, const int64_t *ids, int64_t m, void *stream) {
+    if (!g || (!ids && m > 0)) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (m < 0) return fail(KNN_ERR_INVALID_ARG, "negative m");
+    if (m == 0) return KNN_OK;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    std::vector<int64_t> h((size_t)m);
+    if (is_device_ptr(ids)) {
+        CU(cudaMemcpyAsync(h.data(), ids, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(h.data(), ids, (size_t)m * 8);
+    }
+    for (int64_t v : h)
+        if (v < 0 || v >= g->n) return fail(KNN_ERR_NOT_FOUND, "id %lld not in the graph", (long long)v);
+    int64_t newly = 0;
+    for (int64_t v : h) {
+        uint32_t &w = g->removed_host[(size_t)(v >> 5)];
+        const uint32_t b = 1u << (v & 31);
+        if (!(w & b)) {
+            w |= b;
+            ++newly;
+        }
+    }
+    if (g->n - g->n_removed - newly < 1) return fail(KNN_ERR_INVALID_ARG, "cannot remove every node");
+    CU(cudaMemcpyAsync(g->removed, g->removed_host.data(), g->removed_host.size() * 4, cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    g->n_removed += newly;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_get_edges(knn_graph *g, int64_t *out_ids, float *out_sims, int64_t n_cap,
+                                       int64_t *n_out, void *stream) {
+    if (!g || !out_ids || !n_out) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (n_cap < 0) return fail(KNN_ERR_INVALID_ARG, "negative n_cap");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    const int64_t rows = std::min(n_cap, g->n);
+    const int K = g->p.k;
+    const bool ids_dev = is_device_ptr(out_ids);
+    const bool sims_dev = out_sims == nullptr || is_device_ptr(out_sims);
+    int64_t *tmp_ids = nullptr;
+    float *tmp_sims = nullptr;
+    if (!ids_dev) CU(cudaMallocAsync(&tmp_ids, std::max<size_t>((size_t)rows * K * 8, 16), s));
+    if (out_sims && !sims_dev) CU(cudaMallocAsync(&tmp_sims, std::max<size_t>((size_t)rows * K * 4, 16), s));
+    CU(launch_lists_to_output(g->nbr_ids, g->nbr_d2, rows, K, ids_dev ? out_ids : tmp_ids,
+                              out_sims ? (sims_dev ? out_sims : tmp_sims) : nullptr, s));
+    if (tmp_ids) {
+        CU(cudaMemcpyAsync(out_ids, tmp_ids, (size_t)rows * K * 8, cudaMemcpyDeviceToHost, s));
+        CU(cudaFreeAsync(tmp_ids, s));
+    }
+    if (tmp_sims) {
+        CU(cudaMemcpyAsync(out_sims, tmp_sims, (size_t)rows * K * 4, cudaMemcpyDeviceToHost, s));
+        CU(cudaFreeAsync(tmp_sims, s));
+    }
+    if (tmp_ids || tmp_sims) CU(cudaStreamSynchronize(s));
+    *n_out = rows;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_last_counters(knn_graph *g, int64_t *out, int64_t m, void *stream) {
+    if (!g || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (m < 0 || m > g->last_m) return fail(KNN_ERR_INVALID_ARG, "m exceeds the last call's size");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool dev = is_device_ptr(out);
+    CU(cudaMemcpyAsync(out, g->counters, (size_t)m * NCTR * 8,
+                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!dev) CU(cudaStreamSynchronize(s));
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_stats(knn_graph *g, knn_stats *out) {
+    if (!g || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    DeviceGuard dg(g->device);
+    unsigned long long t[NTOT];
+    unsigned flags[4];
+    CU(cudaStreamSynchronize(g->last_stream));
+    CU(cudaMemcpy(t, g->totals, sizeof t, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(flags, g->small, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags[2] & ERR_OFFER_OVERFLOW) return fail(KNN_ERR_CAPACITY, "Update candidate pool overflowed");
+    std::memset(out, 0, sizeof *out);
+    out->n = g->n;
+    out->capacity = g->p.capacity;
+    out->removed = g->n_removed;
+    out->inserts = g->inserts;
+    out->queries = g->queries;
+    out->search_evals = (int64_t)t[TOT_SEARCH_EVALS];
+    out->update_evals = (int64_t)t[TOT_UPDATE_EVALS];
+    out->cross_evals = (int64_t)t[TOT_CROSS_EVALS];
+    out->rescore_evals = (int64_t)t[TOT_RESCORE_EVALS];
+    out->restarts = (int64_t)t[TOT_RESTARTS];
+    out->moves = (int64_t)t[TOT_MOVES];
+    out->adjacency_reads = (int64_t)t[TOT_ADJ_READS];
+    out->offers = (int64_t)t[TOT_OFFERS];
+    out->device_bytes = (int64_t)g->bytes;
+    return KNN_OK;
+}
+
+KNN_API void knn_graph_destroy(knn_graph *g) {
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    cudaStreamSynchronize(g->last_stream);
+    free_graph(g);
+}
+
+KNN_API knn_status knn_exact_graph(const float *X, int64_t n, int32_t dim, int32_t k, int64_t *out_ids,
+                                   float *out_sims, void *stream) {
+    if (!X || !out_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (dim < 1 || dim > 256) return fail(KNN_ERR_UNSUPPORTED, "dim %d outside 1..256", dim);
+    if (k < 1 || k > 32) return fail(KNN_ERR_UNSUPPORTED, "k %d outside 1..32", k);
+    if (n < k + 1 || n >= (int64_t)INT32_MAX) return fail(KNN_ERR_INVALID_ARG, "need k+1 <= n < 2^31");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int dp = padded_dim(dim);
+    const bool x_dev = is_device_ptr(X);
+    const bool ids_dev = is_device_ptr(out_ids);
+    const bool sims_dev = out_sims == nullptr || is_device_ptr(out_sims);
+    float *rows = nullptr, *d2 = nullptr, *xin = nullptr, *sims_tmp = nullptr;
+    int32_t *ids = nullptr;
+    int64_t *ids_tmp = nullptr;
+    CU(cudaMallocAsync(&rows, (size_t)n * dp * 4, s));
+    CU(cudaMallocAsync(&ids, (size_t)n * k * 4, s));
+    CU(cudaMallocAsync(&d2, (size_t)n * k * 4, s));
+    if (!x_dev) {
+        CU(cudaMallocAsync(&xin, (size_t)n * dim * 4, s));
+        CU(cudaMemcpyAsync(xin, X, (size_t)n * dim * 4, cudaMemcpyHostToDevice, s));
+    }
+    CU(launch_append(x_dev ? X : xin, n, dim, dp, rows, nullptr, nullptr, nullptr, s));
+    ExactArgs ea{};
+    ea.X = rows;
+    ea.removed = nullptr;
+    ea.out_ids = ids;
+    ea.out_d2 = d2;
+    ea.n = n;
+    ea.k = k;
+    CU(launch_exact(dp, ea, s));
+    if (!ids_dev) CU(cudaMallocAsync(&ids_tmp, (size_t)n * k * 8, s));
+    if (out_sims && !sims_dev) CU(cudaMallocAsync(&sims_tmp, (size_t)n * k * 4, s));
+    CU(launch_lists_to_output(ids, d2, n, k, ids_dev ? out_ids : ids_tmp,
+                              out_sims ? (sims_dev ? out_sims : sims_tmp) : nullptr, s));
+    if (ids_tmp) CU(cudaMemcpyAsync(out_ids, ids_tmp, (size_t)n * k * 8, cudaMemcpyDeviceToHost, s));
+    if (sims_tmp) CU(cudaMemcpyAsync(out_sims, sims_tmp, (size_t)n * k * 4, cudaMemcpyDeviceToHost, s));
+    for (void *p : {(void *)rows, (void *)ids, (void *)d2, (void *)xin, (void *)ids_tmp, (void *)sims_tmp})
+        if (p) CU(cudaFreeAsync(p, s));
+    if (ids_tmp || sims_tmp) CU(cudaStreamSynchronize(s));
+    return KNN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// kernels.h -- argument blocks and launchers of the library's CUDA kernels
+// (internal; the public interface is include/knn_graph.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace knn {
+
+// Per-item counters written by the search and update kernels.
+enum Counter : int {
+    CTR_SEARCH_EVALS = 0,  // similarities computed by iGNNS
+    CTR_UPDATE_EVALS = 1,  // Update similarities beyond level 1
+    CTR_RESTARTS = 2,      // restart nodes evaluated
+    CTR_DISCARDED = 3,     // restarts discarded by the expansion test
+    CTR_MOVES = 4,         // eager hill-climbing moves
+    CTR_ADJ_READS = 5,     // neighbour lists scanned
+    CTR_DRAWS = 6,         // restart draws made, free redraws included
+    CTR_PAD = 7,
+    NCTR = 8
+};
+
+// Device-wide running totals (unsigned long long, atomically added).
+enum Total : int {
+    TOT_SEARCH_EVALS = 0,
+    TOT_UPDATE_EVALS,
+    TOT_CROSS_EVALS,
+    TOT_RESCORE_EVALS,
+    TOT_RESTARTS,
+    TOT_MOVES,
+    TOT_ADJ_READS,
+    TOT_OFFERS,
+    TOT_SEARCH_ROW_BYTES,  // bytes of stored rows gathered by searches
+    NTOT = 16
+};
+
+enum ErrorFlag : unsigned {
+    ERR_OFFER_OVERFLOW = 1u,
+};
+
+struct SearchArgs {
+    const uint8_t *rows;         // searched copy, row stride = row bytes of the encoding
+    const float *row_scale;      // FP8: per-row scale
+    const int32_t *nbr;          // adjacency [cap][k]
+    const uint32_t *removed;     // bitset
+    const float *queries;        // padded FP32 query rows
+    int64_t q_stride;            // floats between query rows
+    uint32_t *visited;           // [m][vwords] bitsets, zeroed before the launch
+    int64_t vwords;
+    uint64_t *out_keys;          // [m][KT] sorted (d2 bits << 32 | id)
+    long long *counters;         // [m][NCTR]
+    unsigned long long *totals;  // [NTOT]
+    int32_t m, k, KT;
+    uint32_t n;                  // visible nodes
+    int64_t n_live;              // visible nodes not removed
+    int64_t budget;              // B = max(1, floor(n / speedup))
+    uint64_t max_draws;          // 64 n
+    uint64_t seed;
+    uint64_t stream_base;        // restart stream of item i = stream_base + i
+    float expansion;
+    int32_t discard;             // expansion test enabled
+};
+
+struct RescoreArgs {
+    const float *rows;           // FP32 padded rows
+    const float *queries;
+    int64_t q_stride;
+    const uint64_t *cand_keys;   // [m][KT]
+    uint64_t *out_keys;          // [m][k_out]
+    unsigned long long *totals;
+    int32_t m, KT, k_out;
+};
+
+struct CrossArgs {
+    const float *rows;           // FP32 padded rows; the batch is rows n .. n+m-1
+    const uint64_t *in_keys;     // [m][k] search result of each new point
+    int32_t *nbr_ids;            // lists; rows n .. n+m-1 are written
+    float *nbr_d2;
+    unsigned long long *totals;
+    int32_t m, k;
+    uint32_t n;
+};
+
+struct UpdateArgs {
+    const float *rows;
+    const int32_t *nbr_ids;
+    const float *nbr_d2;
+    const uint32_t *removed;
+    int32_t *head;               // [cap] offer chain heads, -1 = none
+    uint64_t *offer_key;
+    int32_t *offer_next;
+    int32_t *touched;
+    unsigned *offer_count;
+    unsigned *touched_count;
+    unsigned offer_cap;
+    unsigned *error_flags;
+    long long *counters;         // [m][NCTR]
+    unsigned long long *totals;
+    int32_t m, k, depth, hash_size;
+    uint32_t n;                  // graph size before the batch
+};
+
+struct MergeArgs {
+    int32_t *nbr_ids;
+    float *nbr_d2;
+    int32_t *head;
+    const uint64_t *offer_key;
+    const int32_t *offer_next;
+    const int32_t *touched;
+    const unsigned *touched_count;
+    const unsigned *offer_count;
+    unsigned long long *totals;
+    int32_t k;
+};
+
+struct ExactArgs {
+    const float *X;              // padded FP32 rows [n][DP]
+    const uint32_t *removed;     // nullable
+    int32_t *out_ids;            // [n][k]
+    float *out_d2;
+    int64_t n;
+    int32_t k;
+};
+
+// supported padded dimensions
+bool supported_dp(int dp);
+int padded_dim(int d);  // smallest supported DP >= d, or -1
+
+cudaError_t launch_search(int storage, int dp, const SearchArgs &a, cudaStream_t s);
+cudaError_t launch_rescore(int dp, const RescoreArgs &a, cudaStream_t s);
+cudaError_t launch_cross(int dp, const CrossArgs &a, cudaStream_t s);
+cudaError_t launch_update(int dp, const UpdateArgs &a, cudaStream_t s);
+cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t s);
+cudaError_t launch_exact(int dp, const ExactArgs &a, cudaStream_t s);
+
+// small helpers (misc.cu)
+cudaError_t launch_append(const float *in, int64_t m, int d, int dp, float *rows_fp32,
+                          uint16_t *rows_bf16, uint8_t *rows_fp8, float *scale, cudaStream_t s);
+cudaError_t launch_keys_to_output(const uint64_t *keys, int64_t m, int kk, int k_out,
+                                  int64_t *out_ids, float *out_sims, cudaStream_t s);
+cudaError_t launch_lists_to_output(const int32_t *ids, const float *d2, int64_t rows, int k,
+                                   int64_t *out_ids, float *out_sims, cudaStream_t s);
+cudaError_t launch_fill_ids(int64_t *out, int64_t first, int64_t m, cudaStream_t s);
+cudaError_t launch_mark_removed(uint32_t *removed, const int64_t *ids, int64_t m, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t *p, int32_t v, int64_t count, cudaStream_t s);
+
+}  // namespace knn

@@ -1,0 +1,137 @@
+// misc.cu -- storing new rows (with their screening encodings), turning
+// packed keys into the public (id, similarity) form, and small fills.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace knn {
+
+cudaError_t launch_search_fp32(int dp, const SearchArgs &a, cudaStream_t s);
+cudaError_t launch_search_bf16(int dp, const SearchArgs &a, cudaStream_t s);
+cudaError_t launch_search_fp8(int dp, const SearchArgs &a, cudaStream_t s);
+
+bool supported_dp(int dp) {
+    return dp == 16 || dp == 32 || dp == 64 || dp == 96 || dp == 128 || dp == 256;
+}
+
+int padded_dim(int d) {
+    static const int dps[] = {16, 32, 64, 96, 128, 256};
+    for (int dp : dps)
+        if (d <= dp) return dp;
+    return -1;
+}
+
+cudaError_t launch_search(int storage, int dp, const SearchArgs &a, cudaStream_t s) {
+    switch (storage) {
+        case ST_FP32: return launch_search_fp32(dp, a, s);
+        case ST_BF16: return launch_search_bf16(dp, a, s);
+        case ST_FP8: return launch_search_fp8(dp, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// One warp per row: copy d floats into a DP-wide FP32 row (zero padded) and,
+// when asked, the BF16 copy (round to nearest even) or the FP8-E4M3 copy with
+// a per-row scale amax / 448 (code = e4m3(x / scale), round to nearest even,
+// saturating; a zero row gets scale 1).
+__global__ void append_kernel(const float *in, int64_t m, int d, int dp, float *rows,
+                              uint16_t *rows_bf16, uint8_t *rows_fp8, float *scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= m) return;
+    float amax = 0.f;
+    for (int c = lane; c < dp; c += 32) {
+        const float x = c < d ? in[r * d + c] : 0.f;
+        rows[r * dp + c] = x;
+        amax = fmaxf(amax, fabsf(x));
+        if (rows_bf16) rows_bf16[r * dp + c] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    }
+    if (rows_fp8) {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, off));
+        const float sc = amax > 0.f ? __fdiv_rn(amax, 448.0f) : 1.0f;
+        if (lane == 0) scale[r] = sc;
+        for (int c = lane; c < dp; c += 32) {
+            const float x = c < d ? in[r * d + c] : 0.f;
+            rows_fp8[r * dp + c] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(x, sc), __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
+
+cudaError_t launch_append(const float *in, int64_t m, int d, int dp, float *rows_fp32,
+                          uint16_t *rows_bf16, uint8_t *rows_fp8, float *scale, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const int64_t threads = m * 32;
+    append_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(in, m, d, dp, rows_fp32, rows_bf16,
+                                                                   rows_fp8, scale);
+    return cudaGetLastError();
+}
+
+__global__ void keys_to_output_kernel(const uint64_t *keys, int64_t m, int kk, int k_out,
+                                      int64_t *out_ids, float *out_sims) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * k_out) return;
+    const int64_t row = t / k_out, col = t % k_out;
+    const uint64_t key = keys[row * kk + col];
+    out_ids[t] = key == KEY_EMPTY ? -1 : (int64_t)key_id(key);
+    if (out_sims) out_sims[t] = key == KEY_EMPTY ? 0.f : sim_of_d2(key_d2(key));
+}
+
+cudaError_t launch_keys_to_output(const uint64_t *keys, int64_t m, int kk, int k_out,
+                                  int64_t *out_ids, float *out_sims, cudaStream_t s) {
+    const int64_t total = m * k_out;
+    if (total <= 0) return cudaSuccess;
+    keys_to_output_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(keys, m, kk, k_out, out_ids, out_sims);
+    return cudaGetLastError();
+}
+
+__global__ void lists_to_output_kernel(const int32_t *ids, const float *d2, int64_t total,
+                                       int64_t *out_ids, float *out_sims) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int32_t id = ids[t];
+    out_ids[t] = id;
+    if (out_sims) out_sims[t] = id < 0 ? 0.f : sim_of_d2(d2[t]);
+}
+
+cudaError_t launch_lists_to_output(const int32_t *ids, const float *d2, int64_t rows, int k,
+                                   int64_t *out_ids, float *out_sims, cudaStream_t s) {
+    const int64_t total = rows * k;
+    if (total <= 0) return cudaSuccess;
+    lists_to_output_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ids, d2, total, out_ids, out_sims);
+    return cudaGetLastError();
+}
+
+__global__ void fill_ids_kernel(int64_t *out, int64_t first, int64_t m) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) out[t] = first + t;
+}
+
+cudaError_t launch_fill_ids(int64_t *out, int64_t first, int64_t m, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    fill_ids_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(out, first, m);
+    return cudaGetLastError();
+}
+
+__global__ void mark_removed_kernel(uint32_t *removed, const int64_t *ids, int64_t m) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) atomicOr(removed + (ids[t] >> 5), 1u << (ids[t] & 31));
+}
+
+cudaError_t launch_mark_removed(uint32_t *removed, const int64_t *ids, int64_t m, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    mark_removed_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(removed, ids, m);
+    return cudaGetLastError();
+}
+
+__global__ void fill_i32_kernel(int32_t *p, int32_t v, int64_t count) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) p[t] = v;
+}
+
+cudaError_t launch_fill_i32(int32_t *p, int32_t v, int64_t count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    fill_i32_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(p, v, count);
+    return cudaGetLastError();
+}
+
+}  // namespace knn

@@ -1,0 +1,307 @@
+// update.cu -- the Update step (Algorithm 2) for a batch of new points, the
+// intra-batch cross-merge, and the FP32 re-score of screening candidates.
+//
+// Algorithm 2 walks from the neighbours found by the search: each node popped
+// at depth d has its list read (for depth d+1), gets sim(new, node) computed
+// and receives `new` "if needed".  For a batch of m new points this runs in
+// three kernels and never waits on a lock:
+//
+//   cross   one warp per new point: its list = the best k of its search
+//           result and the exact similarities to the other m-1 points of the
+//           batch (in the sequential build a point sees the ones before it;
+//           the batch sees all of them, both ways).
+//   offers  one warp per new point: level 1 is its list (similarities known);
+//           level 2 is the distinct ids of those nodes' lists minus the ones
+//           already seen, minus `new`, minus removed nodes.  Every level reads
+//           lists as they stood before the batch, so no read waits on a write.
+//           A candidate (node, new) that does not beat the node's current
+//           last entry cannot enter its list and is dropped; the others are
+//           pushed onto a per-node chain with atomicExch.
+//   merge   one warp per node that received candidates: the best k of its
+//           list and its chain, written back sorted.  The best k of a set
+//           under a strict total order does not depend on the order the
+//           candidates arrived in, so the result is the same as any sequence
+//           of "if needed, add new" steps.
+//
+// Points of the batch appear in each other's lists through the cross-merge
+// only: the offers kernel offers `new` to nodes that existed before the batch.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace knn {
+
+constexpr int UPD_WARPS = 4;
+
+// ---------------------------------------------------------------------------
+// FP32 re-score of screening candidates (best KT by screening distance).
+// ---------------------------------------------------------------------------
+template <int DP>
+__global__ void __launch_bounds__(UPD_WARPS * 32) rescore_kernel(const RescoreArgs a) {
+    using C = RowCfg<ST_FP32, DP>;
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5);
+    if (item >= a.m) return;
+    float qv[C::QF];
+    load_query<ST_FP32, DP>(a.queries + (size_t)item * a.q_stride, qv);
+    const RowSource src{reinterpret_cast<const uint8_t *>(a.rows), nullptr};
+    WarpTop<1> top;
+    top.init(a.k_out);
+    long long n_scored = 0;
+    for (int c0 = 0; c0 < a.KT; c0 += 32) {
+        const uint64_t ck = (c0 + lane < a.KT) ? a.cand_keys[(size_t)item * a.KT + c0 + lane] : KEY_EMPTY;
+        const int nr = __popc(__ballot_sync(FULL, ck != KEY_EMPTY));  // sorted: empties last
+        if (nr == 0) break;
+        const uint32_t id = key_id(ck);
+        const float d2 = gather_d2<ST_FP32, DP>(src, id, nr, qv);
+        for (int i = 0; i < nr; ++i) {
+            const uint64_t key = pack_key(__shfl_sync(FULL, d2, i), __shfl_sync(FULL, id, i));
+            top.offer(key);
+        }
+        n_scored += nr;
+    }
+    if (lane < a.k_out) a.out_keys[(size_t)item * a.k_out + lane] = top.e[0];
+    if (lane == 0) atomicAdd(a.totals + TOT_RESCORE_EVALS, (unsigned long long)n_scored);
+}
+
+// ---------------------------------------------------------------------------
+// Cross-merge among the points of one batch.
+// ---------------------------------------------------------------------------
+template <int DP>
+__global__ void __launch_bounds__(UPD_WARPS * 32) cross_kernel(const CrossArgs a) {
+    using C = RowCfg<ST_FP32, DP>;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5);
+    if (i >= a.m) return;
+    const uint32_t new_id = a.n + (uint32_t)i;
+    float qv[C::QF];
+    load_query<ST_FP32, DP>(a.rows + (size_t)new_id * DP, qv);
+    const RowSource src{reinterpret_cast<const uint8_t *>(a.rows), nullptr};
+    WarpTop<1> top;
+    top.init(a.k);
+    top.e[0] = lane < a.k ? a.in_keys[(size_t)i * a.k + lane] : KEY_EMPTY;
+    top.worst = top.entry(a.k - 1);
+    for (int j0 = 0; j0 < a.m; j0 += 32) {
+        const int nr = a.m - j0 < 32 ? a.m - j0 : 32;
+        const uint32_t id = a.n + (uint32_t)(j0 + lane);
+        const float d2 = gather_d2<ST_FP32, DP>(src, id, nr, qv);
+        for (int t = 0; t < nr; ++t) {
+            if (j0 + t == i) continue;
+            top.offer(pack_key(__shfl_sync(FULL, d2, t), a.n + (uint32_t)(j0 + t)));
+        }
+    }
+    if (lane < a.k) {
+        const uint64_t key = top.e[0];
+        a.nbr_ids[(size_t)new_id * a.k + lane] = key == KEY_EMPTY ? -1 : (int32_t)key_id(key);
+        a.nbr_d2[(size_t)new_id * a.k + lane] = key == KEY_EMPTY ? __int_as_float(0x7f800000) : key_d2(key);
+    }
+    if (lane == 0 && a.m > 1) atomicAdd(a.totals + TOT_CROSS_EVALS, (unsigned long long)(a.m - 1));
+}
+
+// ---------------------------------------------------------------------------
+// Offers: levels 1 and 2 of Algorithm 2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t list_last_key(const UpdateArgs &a, uint32_t w) {
+    const size_t off = (size_t)w * a.k + (a.k - 1);
+    const int32_t id = __ldg(a.nbr_ids + off);
+    return id < 0 ? KEY_EMPTY : pack_key(__ldg(a.nbr_d2 + off), (uint32_t)id);
+}
+
+// Push the lanes' candidates (has: lane holds one) onto their nodes' chains.
+__device__ __forceinline__ void push_offers(const UpdateArgs &a, bool has, uint32_t w, uint64_t key) {
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(FULL, has);
+    if (bal == 0u) return;
+    const int leader = __ffs(bal) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(a.offer_count, (unsigned)__popc(bal));
+    base = __shfl_sync(FULL, base, leader);
+    if (has) {
+        const unsigned idx = base + (unsigned)__popc(bal & ((1u << lane) - 1u));
+        if (idx < a.offer_cap) {
+            a.offer_key[idx] = key;
+            const int prev = atomicExch(a.head + w, (int)idx);
+            a.offer_next[idx] = prev;
+            if (prev < 0) a.touched[atomicAdd(a.touched_count, 1u)] = (int32_t)w;
+        } else {
+            atomicOr(a.error_flags, (unsigned)ERR_OFFER_OVERFLOW);
+        }
+    }
+}
+
+// Insert into the warp's open-addressing set; true if `v` was not there.
+__device__ __forceinline__ bool hash_insert(uint32_t *table, int size, uint32_t v) {
+    uint32_t h = (v * 0x9E3779B1u) & (uint32_t)(size - 1);
+    for (int probe = 0; probe < size; ++probe) {
+        const uint32_t old = atomicCAS(table + h, 0xffffffffu, v);
+        if (old == 0xffffffffu) return true;
+        if (old == v) return false;
+        h = (h + 1u) & (uint32_t)(size - 1);
+    }
+    return false;  // full: cannot happen, the table holds twice the ids offered
+}
+
+template <int DP>
+__global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const UpdateArgs a) {
+    using C = RowCfg<ST_FP32, DP>;
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int i = blockIdx.x * UPD_WARPS + wib;
+    if (i >= a.m) return;
+    uint32_t *table = smem + (size_t)wib * (a.hash_size + a.k * a.k);
+    uint32_t *frontier = table + a.hash_size;
+
+    const uint32_t new_id = a.n + (uint32_t)i;
+    const RowSource src{reinterpret_cast<const uint8_t *>(a.rows), nullptr};
+
+    // level 1: the new point's list (similarities known from the search)
+    const int32_t lid = lane < a.k ? __ldg(a.nbr_ids + (size_t)new_id * a.k + lane) : -1;
+    const float ld2 = lane < a.k ? __ldg(a.nbr_d2 + (size_t)new_id * a.k + lane) : 0.0f;
+    {
+        bool has = false;
+        uint64_t key = 0;
+        if (lid >= 0 && (uint32_t)lid < a.n &&
+            !((__ldg(a.removed + (lid >> 5)) >> (lid & 31)) & 1u)) {
+            key = pack_key(ld2, new_id);
+            has = key < list_last_key(a, (uint32_t)lid);
+        }
+        push_offers(a, has, (uint32_t)lid, key);
+    }
+
+    long long upd_evals = 0;
+    if (a.depth >= 2) {
+        for (int t = lane; t < a.hash_size; t += 32) table[t] = 0xffffffffu;
+        __syncwarp();
+        if (lane == 0) hash_insert(table, a.hash_size, new_id);
+        if (lid >= 0) hash_insert(table, a.hash_size, (uint32_t)lid);
+        __syncwarp();
+        // level 2 = distinct ids of the level-1 lists, minus seen / new / removed
+        int nf = 0;
+        for (int l = 0; l < a.k; ++l) {
+            const int32_t u = __shfl_sync(FULL, lid, l);
+            if (u < 0) continue;
+            const int32_t w = lane < a.k ? __ldg(a.nbr_ids + (size_t)u * a.k + lane) : -1;
+            bool keep = false;
+            if (w >= 0 && hash_insert(table, a.hash_size, (uint32_t)w))
+                keep = (uint32_t)w < a.n && !((__ldg(a.removed + (w >> 5)) >> (w & 31)) & 1u);
+            const unsigned km = __ballot_sync(FULL, keep);
+            if (keep) frontier[nf + __popc(km & ((1u << lane) - 1u))] = (uint32_t)w;
+            nf += __popc(km);
+        }
+        __syncwarp();
+        float qv[C::QF];
+        load_query<ST_FP32, DP>(a.rows + (size_t)new_id * DP, qv);
+        for (int f0 = 0; f0 < nf; f0 += 32) {
+            const int nr = nf - f0 < 32 ? nf - f0 : 32;
+            const uint32_t w = lane < nr ? frontier[f0 + lane] : 0u;
+            const float d2 = gather_d2<ST_FP32, DP>(src, w, nr, qv);
+            bool has = false;
+            uint64_t key = 0;
+            if (lane < nr) {
+                key = pack_key(d2, new_id);
+                has = key < list_last_key(a, w);
+            }
+            push_offers(a, has, w, key);
+        }
+        upd_evals = nf;
+    }
+    if (lane == 0) {
+        a.counters[(size_t)i * NCTR + CTR_UPDATE_EVALS] = upd_evals;
+        atomicAdd(a.totals + TOT_UPDATE_EVALS, (unsigned long long)upd_evals);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Merge: best k of each touched node's list and its chain of candidates.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(UPD_WARPS * 32) update_merge_kernel(const MergeArgs a) {
+    const int lane = threadIdx.x & 31;
+    const unsigned n_touched = *a.touched_count;
+    const unsigned n_offers = *a.offer_count;
+    const unsigned nwarps = gridDim.x * UPD_WARPS;
+    unsigned long long merged = 0;
+    for (unsigned t = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5); t < n_touched; t += nwarps) {
+        const int32_t w = a.touched[t];
+        const size_t off = (size_t)w * a.k;
+        WarpTop<1> top;
+        top.init(a.k);
+        if (lane < a.k) {
+            const int32_t id = a.nbr_ids[off + lane];
+            top.e[0] = id < 0 ? KEY_EMPTY : pack_key(a.nbr_d2[off + lane], (uint32_t)id);
+        }
+        top.worst = top.entry(a.k - 1);
+        int idx = a.head[w];
+        unsigned steps = 0;
+        while (idx >= 0 && steps < n_offers) {  // a chain never exceeds the offers made
+            top.offer(a.offer_key[idx]);
+            idx = a.offer_next[idx];
+            ++steps;
+        }
+        if (lane < a.k) {
+            const uint64_t key = top.e[0];
+            a.nbr_ids[off + lane] = key == KEY_EMPTY ? -1 : (int32_t)key_id(key);
+            a.nbr_d2[off + lane] = key == KEY_EMPTY ? __int_as_float(0x7f800000) : key_d2(key);
+        }
+        if (lane == 0) a.head[w] = -1;
+        merged += steps;
+    }
+    if (lane == 0 && merged) atomicAdd(a.totals + TOT_OFFERS, merged);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int DP>
+static cudaError_t rescore_dp(const RescoreArgs &a, cudaStream_t s) {
+    rescore_kernel<DP><<<(a.m + UPD_WARPS - 1) / UPD_WARPS, UPD_WARPS * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <int DP>
+static cudaError_t cross_dp(const CrossArgs &a, cudaStream_t s) {
+    cross_kernel<DP><<<(a.m + UPD_WARPS - 1) / UPD_WARPS, UPD_WARPS * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <int DP>
+static cudaError_t update_dp(const UpdateArgs &a, cudaStream_t s) {
+    const size_t smem = (size_t)UPD_WARPS * (a.hash_size + a.k * a.k) * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(update_offers_kernel<DP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    update_offers_kernel<DP><<<(a.m + UPD_WARPS - 1) / UPD_WARPS, UPD_WARPS * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define KNN_DP_DISPATCH(FN, DPVAR, ...)                    \
+    switch (DPVAR) {                                       \
+        case 16: return FN<16>(__VA_ARGS__);               \
+        case 32: return FN<32>(__VA_ARGS__);               \
+        case 64: return FN<64>(__VA_ARGS__);               \
+        case 96: return FN<96>(__VA_ARGS__);               \
+        case 128: return FN<128>(__VA_ARGS__);             \
+        case 256: return FN<256>(__VA_ARGS__);             \
+        default: return cudaErrorInvalidValue;             \
+    }
+
+cudaError_t launch_rescore(int dp, const RescoreArgs &a, cudaStream_t s) {
+    if (a.m <= 0) return cudaSuccess;
+    KNN_DP_DISPATCH(rescore_dp, dp, a, s)
+}
+
+cudaError_t launch_cross(int dp, const CrossArgs &a, cudaStream_t s) {
+    if (a.m <= 0) return cudaSuccess;
+    KNN_DP_DISPATCH(cross_dp, dp, a, s)
+}
+
+cudaError_t launch_update(int dp, const UpdateArgs &a, cudaStream_t s) {
+    if (a.m <= 0) return cudaSuccess;
+    KNN_DP_DISPATCH(update_dp, dp, a, s)
+}
+
+cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t s) {
+    update_merge_kernel<<<sm_count * 16, UPD_WARPS * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace knn

@@ -1,0 +1,269 @@
+"""ctypes binding of the C ABI in include/knn_graph.h.
+
+The functions keep the C names (knn_graph_create, knn_graph_insert_batch,
+...) and only marshal arguments: every step of the method runs in the CUDA
+library.  Arrays may be torch tensors (CUDA or CPU, contiguous) or numpy
+arrays; CUDA tensors pass their device pointer, everything else its host
+pointer, and the library stages host memory itself.  `stream` defaults to
+torch's current CUDA stream.
+
+Importing this module loads libknn_graph.so and raises if it is missing or
+cannot be loaded: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+
+KNN_OK = 0
+KNN_ERR_INVALID_ARG = -1
+KNN_ERR_OOM = -2
+KNN_ERR_CAPACITY = -3
+KNN_ERR_CUDA = -4
+KNN_ERR_DEVICE_TIMEOUT = -5
+KNN_ERR_NOT_FOUND = -6
+KNN_ERR_UNSUPPORTED = -7
+
+KNN_STORAGE_FP32 = 0
+KNN_STORAGE_BF16 = 1
+KNN_STORAGE_FP8_E4M3 = 2
+
+NCOUNTERS = 8
+COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves",
+                 "adjacency_reads", "draws", "pad")
+
+# Every symbol include/knn_graph.h declares.
+EXPORTED = ("knn_graph_create", "knn_graph_insert_batch", "knn_graph_query_batch",
+            "knn_graph_remove", "knn_graph_get_edges", "knn_graph_last_counters",
+            "knn_graph_stats", "knn_graph_destroy", "knn_exact_graph", "knn_last_error",
+            "knn_version")
+
+
+class KnnParams(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("k", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("speedup", ctypes.c_double),
+                ("expansion", ctypes.c_double), ("rescore_mult", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("capacity", ctypes.c_int64)]
+
+
+class KnnStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "n", "capacity", "removed", "inserts", "queries", "search_evals", "update_evals",
+        "cross_evals", "rescore_evals", "restarts", "moves", "adjacency_reads", "offers",
+        "device_bytes")]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class KnnError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+def _load_library() -> ctypes.CDLL:
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sigs = {
+        "knn_graph_create": (I32, [ctypes.POINTER(KnnParams), P, I64, P, ctypes.POINTER(P)]),
+        "knn_graph_insert_batch": (I32, [P, P, I64, P, P, P]),
+        "knn_graph_query_batch": (I32, [P, P, I64, I32, U64, P, P, P]),
+        "knn_graph_remove": (I32, [P, P, I64, P]),
+        "knn_graph_get_edges": (I32, [P, P, P, I64, ctypes.POINTER(I64), P]),
+        "knn_graph_last_counters": (I32, [P, P, I64, P]),
+        "knn_graph_stats": (I32, [P, ctypes.POINTER(KnnStats)]),
+        "knn_graph_destroy": (None, [P]),
+        "knn_exact_graph": (I32, [P, I64, I32, I32, P, P, P]),
+        "knn_last_error": (ctypes.c_char_p, []),
+        "knn_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load_library()
+
+
+def _check(status: int, where: str) -> None:
+    if status != KNN_OK:
+        raise KnnError(status, where, lib.knn_last_error().decode())
+
+
+def _ptr(a) -> int | None:
+    """Data pointer of a torch tensor or numpy array (None stays None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return a.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check_dtype(a, kind: str, name: str):
+    if a is None:
+        return
+    dt = str(a.dtype)
+    if kind not in dt:
+        raise TypeError(f"{name} must be {kind}, got {dt}")
+
+
+# --------------------------------------------------------------------------
+# the C calls, same names
+# --------------------------------------------------------------------------
+
+def knn_graph_create(params: KnnParams, init_vecs, stream=None) -> ctypes.c_void_p:
+    _check_dtype(init_vecs, "float32", "init_vecs")
+    handle = ctypes.c_void_p()
+    _check(lib.knn_graph_create(ctypes.byref(params), _ptr(init_vecs), init_vecs.shape[0],
+                                _stream(stream), ctypes.byref(handle)), "knn_graph_create")
+    return handle
+
+
+def knn_graph_insert_batch(g, vecs, out_ids=None, out_nbrs=None, stream=None) -> None:
+    _check_dtype(vecs, "float32", "vecs")
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_nbrs, "int64", "out_nbrs")
+    _check(lib.knn_graph_insert_batch(g, _ptr(vecs), vecs.shape[0], _ptr(out_ids), _ptr(out_nbrs),
+                                      _stream(stream)), "knn_graph_insert_batch")
+
+
+def knn_graph_query_batch(g, vecs, k_out: int, query_id0: int, out_ids, out_sims=None,
+                          stream=None) -> None:
+    _check_dtype(vecs, "float32", "vecs")
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_sims, "float32", "out_sims")
+    _check(lib.knn_graph_query_batch(g, _ptr(vecs), vecs.shape[0], k_out, query_id0, _ptr(out_ids),
+                                     _ptr(out_sims), _stream(stream)), "knn_graph_query_batch")
+
+
+def knn_graph_remove(g, ids, stream=None) -> None:
+    _check_dtype(ids, "int64", "ids")
+    _check(lib.knn_graph_remove(g, _ptr(ids), ids.shape[0], _stream(stream)), "knn_graph_remove")
+
+
+def knn_graph_get_edges(g, out_ids, out_sims=None, stream=None) -> int:
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_sims, "float32", "out_sims")
+    n_out = ctypes.c_int64()
+    _check(lib.knn_graph_get_edges(g, _ptr(out_ids), _ptr(out_sims), out_ids.shape[0],
+                                   ctypes.byref(n_out), _stream(stream)), "knn_graph_get_edges")
+    return n_out.value
+
+
+def knn_graph_last_counters(g, out, stream=None) -> None:
+    _check_dtype(out, "int64", "out")
+    _check(lib.knn_graph_last_counters(g, _ptr(out), out.shape[0], _stream(stream)),
+           "knn_graph_last_counters")
+
+
+def knn_graph_stats(g) -> dict:
+    st = KnnStats()
+    _check(lib.knn_graph_stats(g, ctypes.byref(st)), "knn_graph_stats")
+    return st.as_dict()
+
+
+def knn_graph_destroy(g) -> None:
+    lib.knn_graph_destroy(g)
+
+
+def knn_exact_graph(X, k: int, out_ids, out_sims=None, stream=None) -> None:
+    _check_dtype(X, "float32", "X")
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_sims, "float32", "out_sims")
+    _check(lib.knn_exact_graph(_ptr(X), X.shape[0], X.shape[1], k, _ptr(out_ids), _ptr(out_sims),
+                               _stream(stream)), "knn_exact_graph")
+
+
+def knn_version() -> str:
+    return lib.knn_version().decode()
+
+
+# --------------------------------------------------------------------------
+# a small owning wrapper
+# --------------------------------------------------------------------------
+
+@dataclass
+class GraphConfig:
+    dim: int
+    k: int = 10
+    depth: int = 2
+    storage: int = KNN_STORAGE_FP32
+    speedup: float = 4.0
+    expansion: float = 5.0
+    rescore_mult: int = 4
+    max_batch: int = 1024
+    seed: int = 4
+    capacity: int = 0
+
+    def params(self) -> KnnParams:
+        return KnnParams(self.dim, self.k, self.depth, self.storage, float(self.speedup),
+                         float(self.expansion), self.rescore_mult, self.max_batch, self.seed,
+                         self.capacity)
+
+
+class Graph:
+    """Owns one knn_graph handle; methods mirror the C calls."""
+
+    def __init__(self, cfg: GraphConfig, init_vecs, stream=None):
+        self.cfg = cfg
+        self.handle = knn_graph_create(cfg.params(), init_vecs, stream)
+
+    def insert(self, vecs, out_ids=None, out_nbrs=None, stream=None):
+        knn_graph_insert_batch(self.handle, vecs, out_ids, out_nbrs, stream)
+
+    def query(self, vecs, k_out, query_id0, out_ids, out_sims=None, stream=None):
+        knn_graph_query_batch(self.handle, vecs, k_out, query_id0, out_ids, out_sims, stream)
+
+    def remove(self, ids, stream=None):
+        knn_graph_remove(self.handle, ids, stream)
+
+    def edges(self, out_ids, out_sims=None, stream=None) -> int:
+        return knn_graph_get_edges(self.handle, out_ids, out_sims, stream)
+
+    def counters(self, out, stream=None):
+        knn_graph_last_counters(self.handle, out, stream)
+
+    def stats(self) -> dict:
+        return knn_graph_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            knn_graph_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

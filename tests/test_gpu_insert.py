@@ -1,0 +1,188 @@
+"""Online inserts (Algorithm 1 = iGNNS + Update) on the GPU against the oracle.
+
+* One point per call: the GPU path must reproduce the sequential oracle
+  exactly -- same search counters, same Update counters, same neighbour list
+  for the new point, and the same whole graph -- up to the first insert whose
+  decisions include a near tie within FP32 rounding.
+* Batches: the edge recall of the GPU graph against the exact graph must be
+  within 0.01 of the sequential oracle's recall on the same stream.
+* Full size (100,000 + 1,024-point batches at d = 128): properties that hold
+  at any size, checked against the oracle one pair at a time.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import cuda_tensor, gather_tol, rel_err
+from paper_1602_06819_gb300.inputs import PLAIN_D128, SMALL_D16, Mixture
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def knn():
+    from paper_1602_06819_gb300 import build
+    build.build()
+    from paper_1602_06819_gb300 import knn as module
+    return module
+
+
+def make_graph(knn, X0, k, speedup, expansion, seed, capacity, max_batch, depth=2, storage=0):
+    cfg = knn.GraphConfig(dim=X0.shape[1], k=k, depth=depth, storage=storage, speedup=speedup,
+                          expansion=expansion, rescore_mult=4, max_batch=max_batch, seed=seed,
+                          capacity=capacity)
+    return knn.Graph(cfg, cuda_tensor(X0))
+
+
+def edges(g, n, k):
+    import torch
+    ids = torch.empty((n, k), dtype=torch.int64, device="cuda")
+    sims = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    assert g.edges(ids, sims) == n
+    return ids.cpu().numpy(), sims.cpu().numpy()
+
+
+@pytest.mark.parametrize("speedup,depth", [(4.0, 2), (20.0, 2), (4.0, 1)])
+def test_single_point_inserts_match_sequential_oracle(knn, speedup, depth):
+    W = SMALL_D16
+    X0, Xs = W.initial(), W.stream(300)
+    k, e, seed = W.k, W.expansion, W.seed_search
+    n0 = X0.shape[0]
+    tol = gather_tol(W.mixture.d)
+
+    # oracle: Algorithm 1 one point at a time, recording each step
+    og = oracle.Graph.exact(X0, k, capacity=n0 + len(Xs))
+    og.X[n0:] = Xs
+    steps = []
+    first_ambiguous = len(Xs)
+    for i in range(len(Xs)):
+        new = n0 + i
+        L = oracle.search(og.X, og.ids[:new], Xs[i], k, speedup, e, seed, new, n=new)
+        og.ids[new], og.sims[new] = L.ids, L.sims
+        u = oracle.update(og.X, new + 1, og.ids, og.sims, new, L.ids, L.sims, depth)
+        steps.append((L.ids.copy(), L.evals, u.evals))
+        if min(L.margin, u.min_margin) < tol:
+            first_ambiguous = i
+            break
+    f = first_ambiguous
+    assert f >= 50, f"only {f} inserts before a near tie"
+
+    import torch
+    g = make_graph(knn, X0, k, speedup, e, seed, n0 + len(Xs), 1, depth)
+    try:
+        ctr = np.empty((1, 8), np.int64)
+        for i in range(f):
+            ids = torch.empty(1, dtype=torch.int64)
+            nbrs = torch.empty((1, k), dtype=torch.int64)
+            g.insert(cuda_tensor(Xs[i:i + 1]), ids, nbrs)
+            g.counters(ctr)
+            L_ids, s_evals, u_evals = steps[i]
+            assert ids[0].item() == n0 + i
+            assert list(nbrs[0].numpy()) == list(L_ids), f"insert {i}: new list"
+            assert (ctr[0, 0], ctr[0, 1]) == (s_evals, u_evals), f"insert {i}: counters"
+        got_ids, got_sims = edges(g, n0 + f, k)
+    finally:
+        g.close()
+    # the oracle graph after exactly f inserts
+    og2 = oracle.Graph.exact(X0, k, capacity=n0 + f)
+    og2.insert_stream(Xs[:f], speedup, e, depth, seed)
+    np.testing.assert_array_equal(got_ids, og2.ids[: n0 + f])
+    assert rel_err(got_sims, og2.sims[: n0 + f]).max() <= 1e-5
+
+
+def _recall(ids, exact):
+    return oracle.correct_edges(ids, exact) / exact.size
+
+
+@pytest.mark.parametrize("batch", [64, 256])
+def test_batched_inserts_recall_matches_sequential(knn, batch):
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=11)
+    n0, na = 4000, 2048
+    X0, Xs = mix.sample(n0, 1), mix.sample(na, 2)
+    k, speedup, e, seed = 10, 4.0, 5.0, 4
+    X = np.vstack([X0, Xs])
+    exact, _, _ = oracle.exact_knn(X, k)
+    og = oracle.Graph.exact(X0, k, capacity=n0 + na)
+    og.insert_stream(Xs, speedup, e, 2, seed)
+    r_seq = _recall(og.ids, exact)
+
+    g = make_graph(knn, X0, k, speedup, e, seed, n0 + na, batch)
+    try:
+        for b0 in range(0, na, batch):
+            g.insert(cuda_tensor(Xs[b0:b0 + batch]))
+        got, sims = edges(g, n0 + na, k)
+        st = g.stats()
+    finally:
+        g.close()
+    r_gpu = _recall(got, exact)
+    assert abs(r_gpu - r_seq) <= 0.01, (r_gpu, r_seq)
+    # every list: k distinct valid ids, no self, true similarities, sorted
+    assert got.min() >= 0 and not np.any(got == np.arange(n0 + na)[:, None])
+    srt = np.sort(got, axis=1)
+    assert not np.any(srt[:, 1:] == srt[:, :-1])
+    assert np.all(np.diff(sims, axis=1) <= 0)
+    for u in np.random.default_rng(0).choice(n0 + na, 40, replace=False):
+        want = [oracle.similarity(X[u], X[v]) for v in got[u]]
+        assert rel_err(sims[u], want).max() <= 1e-5
+    assert st["inserts"] == na and st["update_evals"] <= na * k * k
+
+
+def test_insert_edge_cases(knn):
+    """The smallest graph (n = k+1), a ragged last batch, and a full graph."""
+    import torch
+    mix = Mixture(d=5, components=2, half_width=3.0, sigma=1.0, seed=3)
+    X0, Xs = mix.sample(11, 1), mix.sample(45, 2)
+    g = make_graph(knn, X0, 10, 2.0, 5.0, 1, capacity=56, max_batch=16)
+    try:
+        for b0 in (0, 16, 32):
+            g.insert(cuda_tensor(Xs[b0:b0 + 16]))
+        with pytest.raises(knn.KnnError) as exc:
+            g.insert(cuda_tensor(Xs[:1]))
+        assert exc.value.status == knn.KNN_ERR_CAPACITY
+        with pytest.raises(knn.KnnError):
+            g.insert(cuda_tensor(np.zeros((17, 5), np.float32)))
+        got, _ = edges(g, 56, 10)
+    finally:
+        g.close()
+    X = np.vstack([X0, Xs])
+    assert got.min() >= 0 and got.max() < 56
+    exact, _, _ = oracle.exact_knn(X, 10)
+    assert _recall(got, exact) > 0.8
+
+
+def test_full_size_batch_properties(knn):
+    """100,000 points at d = 128, two 1,024-point batches as the benchmark
+    times them: every search spends exactly B = floor(n/4); Update computes at
+    most k^2 new similarities per point; every list of a new point and of a
+    sample of old points holds k distinct ids with the oracle's similarities,
+    sorted; no old list's k-th similarity decreases."""
+    import torch
+    W = PLAIN_D128
+    X0 = W.initial()
+    Xs = W.stream(2048)
+    k = W.k
+    n0 = X0.shape[0]
+    g = make_graph(knn, X0, k, 4.0, W.expansion, W.seed_search, n0 + 2048, 1024)
+    try:
+        before_ids, before_sims = edges(g, n0, k)
+        ctr = np.empty((1024, 8), np.int64)
+        for b in range(2):
+            g.insert(cuda_tensor(Xs[b * 1024:(b + 1) * 1024]))
+            g.counters(ctr)
+            n = n0 + b * 1024
+            assert np.all(ctr[:, 0] == math.floor(n / 4.0))
+            assert np.all(ctr[:, 1] <= k * k)
+        ids, sims = edges(g, n0 + 2048, k)
+    finally:
+        g.close()
+    X = np.vstack([X0, Xs])
+    assert np.all(sims[:n0, -1] >= before_sims[:, -1])
+    rng = np.random.default_rng(2)
+    rows = np.concatenate([rng.choice(n0, 24, replace=False), n0 + rng.choice(2048, 24, replace=False)])
+    for u in rows:
+        assert len(set(ids[u])) == k and u not in ids[u]
+        want = [oracle.similarity(X[u], X[v]) for v in ids[u]]
+        assert rel_err(sims[u], want).max() <= 1e-5
+        assert np.all(np.diff(sims[u]) <= 0)

@@ -1,0 +1,186 @@
+"""iGNNS queries (Sec. 3) on the GPU against the oracle's sequential search:
+for every query whose decisions all have a margin above the FP32 tolerance,
+the ids, the similarity count (the budget), the restarts, discards, moves and
+draws must be identical.  Covers the FP32, BF16 and FP8-E4M3 searched copies
+(FP32 re-score of the best candidates), removed nodes and the exhaustive
+special case."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import cuda_tensor, gather_tol, rel_err
+from paper_1602_06819_gb300.inputs import PLAIN_D128, Mixture
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def knn():
+    from paper_1602_06819_gb300 import build
+    build.build()
+    from paper_1602_06819_gb300 import knn as module
+    return module
+
+
+def make_graph(knn, X0, k, speedup, expansion, seed, storage=0, rescore_mult=4, max_batch=256,
+               extra=0):
+    cfg = knn.GraphConfig(dim=X0.shape[1], k=k, depth=2, storage=storage, speedup=speedup,
+                          expansion=expansion, rescore_mult=rescore_mult, max_batch=max_batch,
+                          seed=seed, capacity=X0.shape[0] + extra)
+    return knn.Graph(cfg, cuda_tensor(X0))
+
+
+def graph_edges(g, n, k):
+    import torch
+    e = torch.empty((n, k), dtype=torch.int64, device="cuda")
+    assert g.edges(e) == n
+    return e.cpu().numpy()
+
+
+def run_queries(g, Q, k_out, qid0):
+    import torch
+    m = Q.shape[0]
+    ids = torch.empty((m, k_out), dtype=torch.int64, device="cuda")
+    sims = torch.empty((m, k_out), dtype=torch.float32, device="cuda")
+    g.query(cuda_tensor(Q), k_out, qid0, ids, sims)
+    ctr = np.empty((m, 8), np.int64)
+    g.counters(ctr)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), sims.cpu().numpy(), ctr
+
+
+def compare(knn, X0, Q, k, k_out, speedup, e, seed, storage=0, rescore_mult=4, removed=None,
+            max_ambiguous=0.4):
+    n, d = X0.shape
+    o_ids, _, _ = oracle.exact_knn(X0, k)
+    g = make_graph(knn, X0, k, speedup, e, seed, storage, rescore_mult)
+    try:
+        assert np.array_equal(graph_edges(g, n, k), o_ids), "initial graphs differ"
+        rem = None
+        if removed is not None:
+            import torch
+            g.remove(torch.as_tensor(removed, dtype=torch.int64))
+            rem = np.zeros(n, np.uint8)
+            rem[removed] = 1
+        qid0 = 1000
+        ids, sims, ctr = run_queries(g, Q, k_out, qid0)
+    finally:
+        g.close()
+    if storage == 1:
+        _, Xs = oracle.quantize_bf16(X0)
+    elif storage == 2:
+        _, _, Xs = oracle.quantize_e4m3(X0)
+    else:
+        Xs = X0
+    tol = gather_tol(d, storage)
+    ambiguous = 0
+    for i, q in enumerate(Q):
+        kt = k_out if storage == 0 else rescore_mult * k_out
+        r = oracle.search(Xs, o_ids, q, kt, speedup, e, seed, (1 << 63) + qid0 + i, removed=rem)
+        margin = r.margin
+        exp_ids, exp_sims = r.ids, r.sims
+        if storage != 0:
+            exp_ids, exp_sims, m2 = oracle.rescore(X0, q, r.ids, k_out)
+            margin = min(margin, m2)
+        if margin < tol:
+            ambiguous += 1
+            continue
+        assert list(ids[i]) == list(exp_ids), f"query {i}"
+        valid = exp_ids >= 0
+        assert rel_err(sims[i][valid], exp_sims[valid]).max() <= 1e-5
+        got = tuple(ctr[i][[0, 2, 3, 4, 6]])
+        want = (r.evals, r.restarts, r.discarded, r.moves, r.draws)
+        assert got == want, f"query {i}: counters {got} != {want}"
+        assert ctr[i][1] == 0
+    assert ambiguous <= max_ambiguous * len(Q), f"{ambiguous} of {len(Q)} ambiguous"
+    return ambiguous
+
+
+@pytest.mark.parametrize("speedup,e", [(4.0, 5.0), (20.0, 5.0), (8.0, 1.2), (2.0, math.inf)])
+def test_queries_small_d16(knn, speedup, e):
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=11)
+    X0, Q = mix.sample(1000, 1), mix.sample(96, 3)
+    compare(knn, X0, Q, 10, 10, speedup, e, seed=4)
+
+
+def test_queries_d128_many_tiles(knn):
+    mix = Mixture(d=128, components=20, half_width=20.0, sigma=1.0, seed=21)
+    X0, Q = mix.sample(4000, 1), mix.sample(64, 3)
+    compare(knn, X0, Q, 10, 10, 4.0, 5.0, seed=4, max_ambiguous=0.6)
+
+
+def test_queries_ragged_dims_and_k_out(knn):
+    mix = Mixture(d=3, components=5, half_width=10.0, sigma=1.0, seed=2)
+    X0, Q = mix.sample(700, 1), mix.sample(48, 3)
+    compare(knn, X0, Q, 8, 5, 3.0, 2.0, seed=9)
+    mix = Mixture(d=100, components=6, half_width=10.0, sigma=1.0, seed=3)
+    X0, Q = mix.sample(500, 1), mix.sample(32, 3)
+    compare(knn, X0, Q, 10, 10, 2.0, 5.0, seed=9, max_ambiguous=0.6)
+
+
+def test_exhaustive_queries_are_linear_search(knn):
+    """speedup 1 without the expansion test visits every node: the result is
+    the exact k-nn of each query (Sec. 2.1's linear search)."""
+    mix = Mixture(d=32, components=4, half_width=8.0, sigma=1.0, seed=5)
+    X0, Q = mix.sample(300, 1), mix.sample(40, 3)
+    compare(knn, X0, Q, 6, 6, 1.0, math.inf, seed=1)
+
+
+def test_queries_skip_removed_nodes(knn):
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=11)
+    X0, Q = mix.sample(1000, 1), mix.sample(48, 3)
+    removed = np.random.default_rng(0).choice(1000, 150, replace=False)
+    compare(knn, X0, Q, 10, 10, 3.0, 5.0, seed=4, removed=removed)
+    compare(knn, X0, Q[:16], 10, 10, 1.0, math.inf, seed=4, removed=removed)
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_screening_queries(knn, storage):
+    """BF16 / FP8-E4M3 screening with an FP32 re-score of 4k candidates
+    against the oracle searching the same stored values."""
+    mix = Mixture(d=96, components=10, half_width=20.0, sigma=1.0, seed=31)
+    X0, Q = mix.sample(2000, 1), mix.sample(48, 3)
+    compare(knn, X0, Q, 10, 10, 4.0, 5.0, seed=4, storage=storage, max_ambiguous=0.6)
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=11)
+    X0, Q = mix.sample(1000, 1), mix.sample(48, 3)
+    compare(knn, X0, Q, 20, 20, 4.0, 5.0, seed=4, storage=storage, rescore_mult=4)
+
+
+def test_queries_full_size_properties(knn):
+    """The 100,000 x 128 initial graph, in the launch shape of the benchmark
+    (a 1,024-query batch): every query spends exactly B = 25,000 similarity
+    computations, returns k distinct ids sorted by similarity, and each
+    returned similarity equals the oracle's similarity of that pair (checked
+    one by one on a sample)."""
+    X0 = PLAIN_D128.initial()
+    Q = PLAIN_D128.queries(1024)
+    g = make_graph(knn, X0, 10, 4.0, 5.0, PLAIN_D128.seed_search, max_batch=1024)
+    try:
+        ids, sims, ctr = run_queries(g, Q, 10, 0)
+    finally:
+        g.close()
+    assert np.all(ctr[:, 0] == 25_000)
+    assert np.all(ctr[:, 2] >= 1) and np.all(ctr[:, 3] <= ctr[:, 2])
+    srt = np.sort(ids, axis=1)
+    assert ids.min() >= 0 and ids.max() < 100_000 and not np.any(srt[:, 1:] == srt[:, :-1])
+    assert np.all(np.diff(sims, axis=1) <= 0)
+    rng = np.random.default_rng(1)
+    for i in rng.choice(1024, 64, replace=False):
+        for j in range(10):
+            want = oracle.similarity(Q[i], X0[ids[i, j]])
+            assert abs(sims[i, j] - want) <= 1e-5 * want
+
+
+def test_query_results_do_not_depend_on_the_batch(knn):
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=11)
+    X0, Q = mix.sample(1000, 1), mix.sample(64, 3)
+    g = make_graph(knn, X0, 10, 4.0, 5.0, 4)
+    try:
+        all_ids, _, _ = run_queries(g, Q, 10, 500)
+        for s in (0, 17, 40):
+            part, _, _ = run_queries(g, Q[s:s + 9], 10, 500 + s)
+            assert np.array_equal(part, all_ids[s:s + 9])
+    finally:
+        g.close()
