@@ -110,6 +110,18 @@ KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_
                                     int64_t n_init, void *stream, knn_graph **out);
 
 /*
+ * Re-create a graph from a snapshot instead of building its exact graph:
+ * n points and their adjacency lists, e.g. written by knn_graph_get_edges
+ * (checkpoint and resume; not in the paper).  vecs: [n, dim] float32;
+ * nbr_ids: [n, k] int64, each row best first, -1 for an empty slot.  Each
+ * list keeps the order given; the similarities of its entries are
+ * recomputed on the device.  KNN_ERR_INVALID_ARG if an id is outside
+ * -1 .. n-1 or a node lists itself.  Sizes and memory as knn_graph_create.
+ */
+KNN_API knn_status knn_graph_restore(const knn_params *params, const float *vecs, int64_t n,
+                                     const int64_t *nbr_ids, void *stream, knn_graph **out);
+
+/*
  * Insert m points (1 <= m <= max_batch), Algorithm 1 for a batch: every point
  * is searched with iGNNS against the graph as it stood before the call, using
  * the restart stream equal to its new id; the exact similarities among the m

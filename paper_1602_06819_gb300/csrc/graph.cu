@@ -266,11 +266,7 @@ KNN_API const char *knn_last_error(void) { return g_last_error.c_str(); }
 
 KNN_API const char *knn_version(void) { return "knn_graph 0.1 (sm_103a)"; }
 
-KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_vecs, int64_t n_init,
-                                    void *stream, knn_graph **out) {
-    if (!params || !init_vecs || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
-    *out = nullptr;
-    const knn_params &p = *params;
+static knn_status validate_params(const knn_params &p, int64_t n_init) {
     if (p.dim < 1 || p.dim > 256) return fail(KNN_ERR_UNSUPPORTED, "dim %d outside 1..256", p.dim);
     if (p.k < 1 || p.k > 32) return fail(KNN_ERR_UNSUPPORTED, "k %d outside 1..32", p.k);
     if (p.depth < 1 || p.depth > 2) return fail(KNN_ERR_UNSUPPORTED, "depth %d outside 1..2", p.depth);
@@ -284,11 +280,15 @@ KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_
     if (n_init < p.k + 1) return fail(KNN_ERR_INVALID_ARG, "n_init %lld < k + 1", (long long)n_init);
     if (p.capacity < n_init || p.capacity >= (int64_t)INT32_MAX)
         return fail(KNN_ERR_CAPACITY, "capacity %lld must be >= n_init and < 2^31", (long long)p.capacity);
+    return KNN_OK;
+}
 
+// Admission and allocation of everything the graph will ever need, then the
+// initial fills.  On success *out owns the memory; n is still 0.
+static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **out) {
     knn_graph *g = new knn_graph();
     g->p = p;
     if (g->p.storage == KNN_STORAGE_FP32) g->p.rescore_mult = 1;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaGetDevice(&g->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
         delete g;
@@ -302,7 +302,6 @@ KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_
     const int64_t C = p.capacity, M = p.max_batch, K = p.k, DP = g->dp;
     g->offer_cap = (unsigned)(M * (K + K * K));
 
-    // admission: everything the graph will ever need, allocated up front
     size_t need = (size_t)C * DP * 4 + (size_t)C * K * 8 + (size_t)g->vwords * 4 + (size_t)C * 4 +
                   (size_t)M * g->vwords * 4 + (size_t)M * DP * 4 + (size_t)M * p.dim * 4 +
                   (size_t)M * g->KT * 8 + (size_t)M * K * 8 + (size_t)M * NCTR * 8 +
@@ -349,8 +348,7 @@ KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_
         return st;
     }
     g->removed_host.assign((size_t)g->vwords, 0u);
-
-    auto setup = [&]() -> knn_status {
+    auto fills = [&]() -> knn_status {
         CU(cudaMemsetAsync(g->X, 0, (size_t)C * DP * 4, s));
         CU(cudaMemsetAsync(g->removed, 0, (size_t)g->vwords * 4, s));
         CU(cudaMemsetAsync(g->small, 0, 16, s));
@@ -358,6 +356,27 @@ KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_
         CU(cudaMemsetAsync(g->counters, 0, (size_t)M * NCTR * 8, s));
         CU(launch_fill_i32(g->head, -1, C, s));
         CU(launch_fill_i32(g->nbr_ids, -1, C * K, s));
+        return KNN_OK;
+    };
+    st = fills();
+    if (st != KNN_OK) {
+        free_graph(g);
+        return st;
+    }
+    g->last_stream = s;
+    *out = g;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_vecs, int64_t n_init,
+                                    void *stream, knn_graph **out) {
+    if (!params || !init_vecs || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    TRY(validate_params(*params, n_init));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    knn_graph *g = nullptr;
+    TRY(graph_alloc(*params, s, &g));
+    auto build = [&]() -> knn_status {
         TRY(append_rows(g, init_vecs, n_init, 0, g->X, true, s));
         ExactArgs ea{};
         ea.X = g->X;
@@ -365,18 +384,54 @@ KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_
         ea.out_ids = g->nbr_ids;
         ea.out_d2 = g->nbr_d2;
         ea.n = n_init;
-        ea.k = (int32_t)K;
+        ea.k = g->p.k;
         CU(launch_exact(g->dp, ea, s));
         CU(cudaStreamSynchronize(s));
         return KNN_OK;
     };
-    st = setup();
+    knn_status st = build();
     if (st != KNN_OK) {
         free_graph(g);
         return st;
     }
     g->n = n_init;
-    g->last_stream = s;
+    *out = g;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_restore(const knn_params *params, const float *vecs, int64_t n,
+                                     const int64_t *nbr_ids, void *stream, knn_graph **out) {
+    if (!params || !vecs || !nbr_ids || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    TRY(validate_params(*params, n));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    knn_graph *g = nullptr;
+    TRY(graph_alloc(*params, s, &g));
+    auto load = [&]() -> knn_status {
+        TRY(append_rows(g, vecs, n, 0, g->X, true, s));
+        const int64_t K = g->p.k;
+        const int64_t *ids_dev = nbr_ids;
+        int64_t *tmp = nullptr;
+        if (!is_device_ptr(nbr_ids)) {
+            CU(cudaMallocAsync(&tmp, (size_t)n * K * 8, s));
+            CU(cudaMemcpyAsync(tmp, nbr_ids, (size_t)n * K * 8, cudaMemcpyHostToDevice, s));
+            ids_dev = tmp;
+        }
+        CU(launch_restore_lists(g->dp, g->X, ids_dev, n, (int)K, g->nbr_ids, g->nbr_d2, g->small + 3, s));
+        if (tmp) CU(cudaFreeAsync(tmp, s));
+        unsigned bad = 0;
+        CU(cudaMemcpyAsync(&bad, g->small + 3, sizeof bad, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (bad) return fail(KNN_ERR_INVALID_ARG, "snapshot lists hold an id outside -1..n-1, a self "
+                                                  "edge or an entry after an empty slot");
+        return KNN_OK;
+    };
+    knn_status st = load();
+    if (st != KNN_OK) {
+        free_graph(g);
+        return st;
+    }
+    g->n = n;
     *out = g;
     return KNN_OK;
 }

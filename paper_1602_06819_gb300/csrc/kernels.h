@@ -132,6 +132,9 @@ cudaError_t launch_cross(int dp, const CrossArgs &a, cudaStream_t s);
 cudaError_t launch_update(int dp, const UpdateArgs &a, cudaStream_t s);
 cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t s);
 cudaError_t launch_exact(int dp, const ExactArgs &a, cudaStream_t s);
+// snapshot restore: copy int64 lists (checking every id) and recompute their d2
+cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,
+                                 int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s);
 
 // small helpers (misc.cu)
 cudaError_t launch_append(const float *in, int64_t m, int d, int dp, float *rows_fp32,

@@ -249,6 +249,38 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) update_merge_kernel(const Merg
 }
 
 // ---------------------------------------------------------------------------
+// Snapshot restore: one warp per node copies its list (checking each id) and
+// recomputes the squared distances of the entries, keeping the given order.
+// ---------------------------------------------------------------------------
+template <int DP>
+__global__ void __launch_bounds__(UPD_WARPS * 32)
+restore_lists_kernel(const float *rows, const int64_t *in_ids, int64_t n, int k, int32_t *nbr_ids,
+                     float *nbr_d2, unsigned *bad) {
+    using C = RowCfg<ST_FP32, DP>;
+    const int lane = threadIdx.x & 31;
+    const int64_t u = (int64_t)blockIdx.x * UPD_WARPS + (threadIdx.x >> 5);
+    if (u >= n) return;
+    int64_t v = lane < k ? in_ids[u * k + lane] : -1;
+    if (lane < k && (v < -1 || v >= n || v == u)) {
+        atomicOr(bad, 1u);
+        v = -1;
+    }
+    // entries are gathered in list order; empty slots sit at the end
+    const unsigned valid = __ballot_sync(FULL, v >= 0);
+    const int nv = __popc(valid);
+    float qv[C::QF];
+    load_query<ST_FP32, DP>(rows + u * DP, qv);
+    const RowSource src{reinterpret_cast<const uint8_t *>(rows), nullptr};
+    const float d2 = gather_d2<ST_FP32, DP>(src, (uint32_t)(v < 0 ? 0 : v), nv, qv);
+    if (lane < k) {
+        const bool ok = v >= 0 && lane < nv && ((valid >> lane) & 1u);
+        nbr_ids[u * k + lane] = ok ? (int32_t)v : -1;
+        nbr_d2[u * k + lane] = ok ? d2 : __int_as_float(0x7f800000);
+        if (v >= 0 && !ok) atomicOr(bad, 2u);  // an entry after an empty slot
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 template <int DP>
@@ -297,6 +329,20 @@ cudaError_t launch_cross(int dp, const CrossArgs &a, cudaStream_t s) {
 cudaError_t launch_update(int dp, const UpdateArgs &a, cudaStream_t s) {
     if (a.m <= 0) return cudaSuccess;
     KNN_DP_DISPATCH(update_dp, dp, a, s)
+}
+
+template <int DP>
+static cudaError_t restore_dp(const float *rows, const int64_t *in_ids, int64_t n, int k, int32_t *nbr_ids,
+                              float *nbr_d2, unsigned *bad, cudaStream_t s) {
+    restore_lists_kernel<DP><<<(unsigned)((n + UPD_WARPS - 1) / UPD_WARPS), UPD_WARPS * 32, 0, s>>>(
+        rows, in_ids, n, k, nbr_ids, nbr_d2, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,
+                                 int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    KNN_DP_DISPATCH(restore_dp, dp, rows, in_ids, n, k, nbr_ids, nbr_d2, bad, s)
 }
 
 cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t s) {

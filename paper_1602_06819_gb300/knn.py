@@ -40,7 +40,7 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
                  "adjacency_reads", "draws", "pad")
 
 # Every symbol include/knn_graph.h declares.
-EXPORTED = ("knn_graph_create", "knn_graph_insert_batch", "knn_graph_query_batch",
+EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
             "knn_graph_remove", "knn_graph_get_edges", "knn_graph_last_counters",
             "knn_graph_stats", "knn_graph_destroy", "knn_exact_graph", "knn_last_error",
             "knn_version")
@@ -78,6 +78,7 @@ def _load_library() -> ctypes.CDLL:
     P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
     sigs = {
         "knn_graph_create": (I32, [ctypes.POINTER(KnnParams), P, I64, P, ctypes.POINTER(P)]),
+        "knn_graph_restore": (I32, [ctypes.POINTER(KnnParams), P, I64, P, P, ctypes.POINTER(P)]),
         "knn_graph_insert_batch": (I32, [P, P, I64, P, P, P]),
         "knn_graph_query_batch": (I32, [P, P, I64, I32, U64, P, P, P]),
         "knn_graph_remove": (I32, [P, P, I64, P]),
@@ -141,6 +142,15 @@ def knn_graph_create(params: KnnParams, init_vecs, stream=None) -> ctypes.c_void
     handle = ctypes.c_void_p()
     _check(lib.knn_graph_create(ctypes.byref(params), _ptr(init_vecs), init_vecs.shape[0],
                                 _stream(stream), ctypes.byref(handle)), "knn_graph_create")
+    return handle
+
+
+def knn_graph_restore(params: KnnParams, vecs, nbr_ids, stream=None) -> ctypes.c_void_p:
+    _check_dtype(vecs, "float32", "vecs")
+    _check_dtype(nbr_ids, "int64", "nbr_ids")
+    handle = ctypes.c_void_p()
+    _check(lib.knn_graph_restore(ctypes.byref(params), _ptr(vecs), vecs.shape[0], _ptr(nbr_ids),
+                                 _stream(stream), ctypes.byref(handle)), "knn_graph_restore")
     return handle
 
 
@@ -229,9 +239,13 @@ class GraphConfig:
 class Graph:
     """Owns one knn_graph handle; methods mirror the C calls."""
 
-    def __init__(self, cfg: GraphConfig, init_vecs, stream=None):
+    def __init__(self, cfg: GraphConfig, init_vecs, stream=None, nbr_ids=None):
+        """Exact initial graph of init_vecs, or, with nbr_ids, a restored one."""
         self.cfg = cfg
-        self.handle = knn_graph_create(cfg.params(), init_vecs, stream)
+        if nbr_ids is None:
+            self.handle = knn_graph_create(cfg.params(), init_vecs, stream)
+        else:
+            self.handle = knn_graph_restore(cfg.params(), init_vecs, nbr_ids, stream)
 
     def insert(self, vecs, out_ids=None, out_nbrs=None, stream=None):
         knn_graph_insert_batch(self.handle, vecs, out_ids, out_nbrs, stream)

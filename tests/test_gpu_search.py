@@ -25,11 +25,14 @@ def knn():
 
 
 def make_graph(knn, X0, k, speedup, expansion, seed, storage=0, rescore_mult=4, max_batch=256,
-               extra=0):
+               extra=0, nbr_ids=None):
+    """A GPU graph over X0: its exact graph built on the GPU, or, given
+    nbr_ids, the oracle's lists restored (so both sides search one graph)."""
     cfg = knn.GraphConfig(dim=X0.shape[1], k=k, depth=2, storage=storage, speedup=speedup,
                           expansion=expansion, rescore_mult=rescore_mult, max_batch=max_batch,
                           seed=seed, capacity=X0.shape[0] + extra)
-    return knn.Graph(cfg, cuda_tensor(X0))
+    return knn.Graph(cfg, cuda_tensor(X0),
+                     nbr_ids=None if nbr_ids is None else cuda_tensor(nbr_ids))
 
 
 def graph_edges(g, n, k):
@@ -55,9 +58,9 @@ def compare(knn, X0, Q, k, k_out, speedup, e, seed, storage=0, rescore_mult=4, r
             max_ambiguous=0.4):
     n, d = X0.shape
     o_ids, _, _ = oracle.exact_knn(X0, k)
-    g = make_graph(knn, X0, k, speedup, e, seed, storage, rescore_mult)
+    g = make_graph(knn, X0, k, speedup, e, seed, storage, rescore_mult, nbr_ids=o_ids)
     try:
-        assert np.array_equal(graph_edges(g, n, k), o_ids), "initial graphs differ"
+        assert np.array_equal(graph_edges(g, n, k), o_ids), "restored lists differ"
         rem = None
         if removed is not None:
             import torch
@@ -171,6 +174,32 @@ def test_queries_full_size_properties(knn):
         for j in range(10):
             want = oracle.similarity(Q[i], X0[ids[i, j]])
             assert abs(sims[i, j] - want) <= 1e-5 * want
+
+
+def test_restore_keeps_lists_and_checks_ids(knn):
+    import torch
+    mix = Mixture(d=16, components=4, half_width=6.0, sigma=1.0, seed=2)
+    X0 = mix.sample(300, 1)
+    o_ids, o_sims, _ = oracle.exact_knn(X0, 7)
+    g = make_graph(knn, X0, 7, 4.0, 5.0, 1, nbr_ids=o_ids)
+    try:
+        ids = torch.empty((300, 7), dtype=torch.int64, device="cuda")
+        sims = torch.empty((300, 7), dtype=torch.float32, device="cuda")
+        assert g.edges(ids, sims) == 300
+        assert np.array_equal(ids.cpu().numpy(), o_ids)
+        assert rel_err(sims.cpu().numpy(), o_sims).max() <= 1e-5
+    finally:
+        g.close()
+    for bad in (300, -2):
+        b = o_ids.copy()
+        b[5, 3] = bad
+        with pytest.raises(knn.KnnError) as exc:
+            make_graph(knn, X0, 7, 4.0, 5.0, 1, nbr_ids=b)
+        assert exc.value.status == knn.KNN_ERR_INVALID_ARG
+    b = o_ids.copy()
+    b[9, 0] = 9
+    with pytest.raises(knn.KnnError):
+        make_graph(knn, X0, 7, 4.0, 5.0, 1, nbr_ids=b)
 
 
 def test_query_results_do_not_depend_on_the_batch(knn):
