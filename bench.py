@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Benchmark of the online k-nn graph build (Debatty et al., KDD'16).
+
+Workload (the d = 128 plain FP32 configuration): an exact initial graph of
+100,000 points drawn from a 100-component isotropic Gaussian mixture (means
+uniform in [-20, 20]^128, sigma 1), k = 10, then a stream of points from the
+same mixture inserted in batches of 1,024 (Algorithm 1 per batch: iGNNS with
+a budget of n/speedup similarities, expansion 5, then Update to DEPTH 2).
+
+A step is one insert batch of 1,024 points: store, search, intra-batch merge,
+Update.  W untimed steps, then K timed steps, each timed with CUDA events on
+the stream the library launches on, the L2 flushed between steps.  The
+default K + W = 98 batches insert 100,352 points.  One JSON line on stdout.
+
+    python bench.py [--steps K] [--warmup W] [--speedup S] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on this machine's cores instead.
+Under torchrun each rank runs an independent replica (its own stream seed);
+the value is the inserts of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "inserts+queries/sec at edge recall≥0.95 vs exact; p50/p99 latency; HBM GB/s"
+UNIT = "inserts/s"
+RECALL_TARGET = 0.95
+FALLBACK_HBM_GBS = 6800.0
+SEARCH_PROFILE = os.path.join(ROOT, "profiles", "ignns_search_fp32_d128_n100k_batch1024.md")
+SEARCH_SOURCES = ("common.cuh", "search.cuh", "search_fp32.cu")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=95)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--speedup", type=float, default=4.0)
+    ap.add_argument("--expansion", type=float, default=5.0)
+    ap.add_argument("--depth", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def search_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in SEARCH_SOURCES:
+        with open(os.path.join(ROOT, "paper_1602_06819_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per search launch from the committed ncu summary, if that
+    summary was taken on the current search kernel source."""
+    try:
+        text = open(SEARCH_PROFILE).read()
+    except OSError:
+        return None, None
+    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != search_source_hash():
+        return None, None
+    return float(m_tr.group(1)), os.path.relpath(SEARCH_PROFILE, ROOT)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in out.splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def edge_recall(torch, ids, exact):
+    """Directed edges u->v present in both graphs, over n*k (Sec. 8.5's e_c)."""
+    hit = 0
+    for r0 in range(0, ids.shape[0], 16384):
+        a, b = ids[r0:r0 + 16384], exact[r0:r0 + 16384]
+        hit += int((a[:, :, None] == b[:, None, :]).any(-1).sum().item())
+    return hit
+
+
+def quality_q(e_c, n, n_a, k):
+    e_m = n_a * k + n * k * n_a / (n_a + n)
+    e_u = (n + n_a) * k - e_m
+    return (e_c - e_u) / e_m
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle, timed (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_setup(W, n_sample=20000):
+    """Untimed setup of the oracle sample: the exact graph of the first
+    n_sample points of the initial set, built by the oracle itself."""
+    import oracle
+    oracle.build()
+    X0 = W.initial()[:n_sample]
+    g = oracle.Graph.exact(X0, W.k, capacity=n_sample + 40000)
+    return g
+
+
+def oracle_cores() -> int:
+    return 1  # Algorithm 1 is sequential: the timed inserts use one thread
+
+
+def run_cpu_baseline(args, W, n_full_avg):
+    """Sequential oracle (Algorithm 1, FP64) on a prefix of the workload."""
+    g = oracle_sample_setup(W)
+    Xs = W.stream(40000)
+    n_start = g.n
+    done, t0 = 0, time.perf_counter()
+    while done < 32768 and time.perf_counter() - t0 < args.cpu_seconds:
+        g.insert_stream(Xs[done:done + 256], args.speedup, args.expansion, args.depth,
+                        W.seed_search)
+        done += 256
+    dt = time.perf_counter() - t0
+    rate = done / dt
+    n_avg = n_start + done / 2
+    return {
+        "value": rate * n_avg / n_full_avg, "unit": UNIT, "cores": oracle_cores(),
+        "kind": "oracle",
+        "sample": (f"FP64 oracle, Algorithm 1 one point at a time on 1 thread: {done} stream "
+                   f"points into the exact graph of the first {n_start} initial points "
+                   f"(speedup {args.speedup:g}, e {args.expansion:g}, DEPTH {args.depth}) in "
+                   f"{dt:.1f} s = {rate:.1f} inserts/s at mean n {n_avg:.0f}; scaled by "
+                   f"{n_avg:.0f}/{n_full_avg:.0f} (the iGNNS cost of an insert is "
+                   f"n/speedup similarities) to the timed GPU region's mean n"),
+        "measured_inserts_per_s": rate,
+    }
+
+
+def run_reference(args, W):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_full_avg = W.n_init + (args.warmup + args.steps / 2) * W.batch
+    g = oracle_sample_setup(W)
+    Xs = W.stream(40000)
+    per_step = 64
+    pos = 0
+    for _ in range(args.warmup):
+        g.insert_stream(Xs[pos:pos + per_step], args.speedup, args.expansion, args.depth,
+                        W.seed_search)
+        pos += per_step
+    n_start = g.n
+    step_s = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        g.insert_stream(Xs[pos:pos + per_step], args.speedup, args.expansion, args.depth,
+                        W.seed_search)
+        step_s.append(time.perf_counter() - t0)
+        pos += per_step
+    total = sum(step_s)
+    rate = args.steps * per_step / total
+    n_avg = n_start + args.steps * per_step / 2
+    value = rate * n_avg / n_full_avg
+    sample = (f"FP64 oracle, Algorithm 1 on 1 thread: each step inserts {per_step} stream "
+              f"points one at a time into the oracle's own graph (exact graph of the first "
+              f"20000 initial points, then the inserts so far); "
+              f"{rate:.1f} inserts/s at mean n {n_avg:.0f}, scaled by n/speedup to the GPU "
+              f"run's mean n {n_full_avg:.0f}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, W),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_cores(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, W):
+    return {"workload": W.name, "n_init": W.n_init, "d": W.mixture.d, "k": W.k,
+            "components": W.mixture.components, "batch": W.batch,
+            "speedup": args.speedup, "expansion": args.expansion, "depth": args.depth,
+            "similarity": "1/(1+L2)", "inserts_timed_per_gpu": args.steps * W.batch,
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    from paper_1602_06819_gb300.inputs import PLAIN_D128 as W
+    if args.impl == "reference":
+        run_reference(args, W)
+        return
+
+    import numpy as np
+    import torch
+    from paper_1602_06819_gb300 import build as kbuild
+    kbuild.build()
+    from paper_1602_06819_gb300 import knn
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    K, Wm, B = args.steps, args.warmup, W.batch
+    n_stream = (K + Wm) * B
+    X0 = torch.from_numpy(W.initial()).cuda()
+    Xs_host = W.mixture.sample(n_stream, W.seed_stream + 1000 * rank)
+    Xs = torch.from_numpy(Xs_host).cuda()
+    capacity = W.n_init + n_stream
+    cfg = knn.GraphConfig(dim=W.mixture.d, k=W.k, depth=args.depth, speedup=args.speedup,
+                          expansion=args.expansion, max_batch=B, seed=W.seed_search + rank,
+                          capacity=capacity)
+
+    # exact initial graph (timed on its own, not part of a step)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    g = knn.Graph(cfg, X0)
+    e1.record()
+    torch.cuda.synchronize()
+    exact_ms = e0.elapsed_time(e1)
+    g.set_timing(True)
+
+    for i in range(Wm):
+        g.insert(Xs[i * B:(i + 1) * B])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    phases = {p: 0.0 for p in knn.PHASES}
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    st0 = g.stats()
+    n_before = st0["n"]
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.fill_(float(i))
+        a, b = ev[i]
+        a.record()
+        g.insert(Xs[(Wm + i) * B:(Wm + i + 1) * B])
+        b.record()
+        for p, v in g.last_timing().items():
+            phases[p] += v
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    st1 = g.stats()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    inserts = K * B * world
+    value = inserts / (total_ms / 1e3)
+
+    # edge recall and Q of the final graph against its exact graph (Sec. 8.5)
+    n_final = st1["n"]
+    Xall = torch.cat([X0, Xs[:n_final - W.n_init]])
+    exact = torch.empty((n_final, W.k), dtype=torch.int64, device="cuda")
+    knn.knn_exact_graph(Xall, W.k, exact)
+    online = torch.empty((n_final, W.k), dtype=torch.int64, device="cuda")
+    g.edges(online)
+    e_c = edge_recall(torch, online, exact)
+    recall = e_c / exact.numel()
+    q = quality_q(e_c, W.n_init, n_final - W.n_init, W.k)
+    del exact, online, Xall
+
+    # roofline of the dominant kernel (the iGNNS search)
+    row_bytes = 4 * 128
+    d_evals = st1["search_evals"] - st0["search_evals"]
+    d_adj = st1["adjacency_reads"] - st0["adjacency_reads"]
+    alg_bytes_launch = (d_evals * row_bytes + d_adj * W.k * 4 + K * B * row_bytes) / K
+    search_ms = phases["search"] / K
+    achieved = alg_bytes_launch / (search_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic, traffic_src = profiled_traffic()
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    g.close()
+    del g
+
+    # end to end through the C ABI with host buffers (fresh graph, same batches)
+    e2e = None
+    if not args.no_e2e:
+        g2 = knn.Graph(cfg, X0)
+        Xp = torch.from_numpy(Xs_host).pin_memory()
+        ids_h = torch.empty(B, dtype=torch.int64).pin_memory()
+        nbrs_h = torch.empty((B, W.k), dtype=torch.int64).pin_memory()
+        for i in range(Wm):
+            g2.insert(Xp[i * B:(i + 1) * B], ids_h, nbrs_h)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(K):
+            g2.insert(Xp[(Wm + i) * B:(Wm + i + 1) * B], ids_h, nbrs_h)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([wall], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        g2.close()
+        e2e = {"value": inserts / wall, "unit": UNIT,
+               "h2d_bytes_per_step": B * W.mixture.d * 4,
+               "d2h_bytes_per_step": B * W.k * 8}
+
+    cpu = None
+    n_full_avg = n_before + K * B / 2
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(args, W, n_full_avg)
+
+    if rank == 0:
+        srt = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, W),
+            "recall": {"edge_recall": recall, "target": RECALL_TARGET,
+                       "target_met": recall >= RECALL_TARGET, "Q": q, "n_final": n_final},
+            "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                           "unit": "one 1,024-point insert batch"},
+            "evals_per_insert": {"search": d_evals / (K * B),
+                                 "update": (st1["update_evals"] - st0["update_evals"]) / (K * B),
+                                 "cross": (st1["cross_evals"] - st0["cross_evals"]) / (K * B)},
+            "phases_ms_per_step": {p: v / K for p, v in phases.items()},
+            "exact_build_ms": exact_ms,
+            "roofline": {"kernel": "ignns_search_kernel<fp32,128>", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
+                         "traffic": traffic, "traffic_source": traffic_src,
+                         "algorithmic_bytes_per_launch": alg_bytes_launch,
+                         "launch_ms": search_ms},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

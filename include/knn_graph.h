@@ -95,7 +95,19 @@ typedef struct knn_stats {
     int64_t adjacency_reads; /* neighbour lists scanned by the climbs              */
     int64_t offers;          /* candidate (node, new) pairs merged by Update        */
     int64_t device_bytes;    /* device memory held by the graph                    */
+    int64_t kernel_launches; /* kernels this library launched for the graph        */
 } knn_stats;
+
+/* Phases of an insert or query call, in order, for knn_graph_last_timing. */
+typedef enum knn_phase {
+    KNN_PHASE_STORE = 0,   /* copy in, pad and encode the new rows           */
+    KNN_PHASE_SEARCH = 1,  /* iGNNS (Sec. 3), visited sets cleared first      */
+    KNN_PHASE_RESCORE = 2, /* FP32 re-score of screening candidates           */
+    KNN_PHASE_CROSS = 3,   /* similarities among the points of the batch      */
+    KNN_PHASE_OFFERS = 4,  /* Update levels 1..DEPTH: candidates per node      */
+    KNN_PHASE_MERGE = 5,   /* Update: merge candidates into the lists          */
+    KNN_NUM_PHASES = 6
+} knn_phase;
 
 typedef struct knn_graph knn_graph; /* opaque, owned by the library */
 
@@ -172,6 +184,21 @@ KNN_API knn_status knn_graph_get_edges(knn_graph *g, int64_t *out_ids, float *ou
  */
 KNN_API knn_status knn_graph_last_counters(knn_graph *g, int64_t *out, int64_t m,
                                            void *stream);
+
+/*
+ * Per-phase timing with CUDA events recorded on the call's stream around
+ * each phase of every later insert and query call (enable = 1), or none
+ * (enable = 0, the default).
+ */
+KNN_API knn_status knn_graph_set_timing(knn_graph *g, int32_t enable);
+
+/*
+ * Milliseconds each knn_phase took in the last insert or query call
+ * (synchronises that call's stream; phases the call did not run read 0).
+ * out_ms: host [n] float, n <= KNN_NUM_PHASES.  KNN_ERR_INVALID_ARG if
+ * timing is off.
+ */
+KNN_API knn_status knn_graph_last_timing(knn_graph *g, float *out_ms, int32_t n);
 
 /* Running totals (synchronises the graph's last stream). */
 KNN_API knn_status knn_graph_stats(knn_graph *g, knn_stats *out);

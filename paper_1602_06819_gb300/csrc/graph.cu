@@ -66,7 +66,20 @@ struct knn_graph {
     int64_t *out_ids_dev = nullptr;
     float *out_sims_dev = nullptr;
     cudaStream_t last_stream = nullptr;
+    int64_t launches = 0;          // kernels launched by this library for the graph
+    bool timing = false;           // record events around each phase
+    cudaEvent_t ev[KNN_NUM_PHASES + 1] = {};
+    bool phase_ran[KNN_NUM_PHASES] = {};
 };
+
+// Mark the start of phase `ph` (and the end of the previous one).
+static void phase_mark(knn_graph *g, int ph, cudaStream_t s) {
+    if (!g->timing) return;
+    cudaEventRecord(g->ev[ph], s);
+}
+static void phase_begin_call(knn_graph *g) {
+    for (bool &r : g->phase_ran) r = false;
+}
 
 // ---------------------------------------------------------------------------
 // errors
@@ -142,6 +155,8 @@ static knn_status dev_alloc(knn_graph *g, T **ptr, size_t count) {
 
 static void free_graph(knn_graph *g) {
     for (void *p : g->allocations) cudaFree(p);
+    for (cudaEvent_t e : g->ev)
+        if (e) cudaEventDestroy(e);
     delete g;
 }
 
@@ -165,6 +180,7 @@ static knn_status append_rows(knn_graph *g, const float *vecs, int64_t m, int64_
             src = g->stage_in;
         }
         const int64_t r = first + c0;
+        ++g->launches;
         CU(launch_append(src, cm, d, dp, dst_rows + r * dp,
                          (screening && g->Xb) ? g->Xb + r * dp : nullptr,
                          (screening && g->X8) ? g->X8 + r * dp : nullptr,
@@ -214,6 +230,9 @@ static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int 
     a.discard = (e > 0.0 && std::isfinite(e)) ? 1 : 0;
     a.expansion = a.discard ? (float)e : 1.0f;
     CU(launch_search(g->p.storage, g->dp, a, s));
+    ++g->launches;
+    g->phase_ran[KNN_PHASE_SEARCH] = true;
+    phase_mark(g, KNN_PHASE_RESCORE, s);
     if (!screening) {
         *keys_out = g->keys_search;
         return KNN_OK;
@@ -229,6 +248,8 @@ static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int 
     r.KT = KT;
     r.k_out = k_out;
     CU(launch_rescore(g->dp, r, s));
+    ++g->launches;
+    g->phase_ran[KNN_PHASE_RESCORE] = true;
     *keys_out = g->keys_final;
     return KNN_OK;
 }
@@ -241,6 +262,7 @@ static knn_status emit_keys(knn_graph *g, const uint64_t *keys, int64_t m, int k
     int64_t *ids_target = ids_dev ? out_ids : g->out_ids_dev;
     float *sims_target = out_sims ? (sims_dev ? out_sims : g->out_sims_dev) : nullptr;
     CU(launch_keys_to_output(keys, m, kk, k_out, ids_target, sims_target, s));
+    ++g->launches;
     bool need_sync = false;
     if (!ids_dev) {
         CU(cudaMemcpyAsync(out_ids, g->out_ids_dev, (size_t)m * k_out * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -447,12 +469,17 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     g->last_stream = s;
     const int64_t n0 = g->n;
     const int K = g->p.k;
+    phase_begin_call(g);
 
     // a1: store the new rows (and their screening copy)
+    phase_mark(g, KNN_PHASE_STORE, s);
     TRY(append_rows(g, vecs, m, n0, g->X, true, s));
+    g->phase_ran[KNN_PHASE_STORE] = true;
     // a2-a5: iGNNS of every new point against the n0 nodes before the batch
+    phase_mark(g, KNN_PHASE_SEARCH, s);
     const uint64_t *keys = nullptr;
     TRY(run_search(g, g->X + n0 * g->dp, m, K, (uint64_t)n0, s, &keys));
+    phase_mark(g, KNN_PHASE_CROSS, s);
     // a6: exact similarities among the batch, written as the new lists
     CrossArgs ca{};
     ca.rows = g->X;
@@ -464,7 +491,10 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     ca.k = K;
     ca.n = (uint32_t)n0;
     CU(launch_cross(g->dp, ca, s));
+    ++g->launches;
+    g->phase_ran[KNN_PHASE_CROSS] = true;
     // a7-a8: Update (Algorithm 2): collect candidates, then merge them
+    phase_mark(g, KNN_PHASE_OFFERS, s);
     CU(cudaMemsetAsync(g->small, 0, 2 * sizeof(unsigned), s));
     UpdateArgs ua{};
     ua.rows = g->X;
@@ -487,6 +517,9 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     ua.hash_size = g->hash_size;
     ua.n = (uint32_t)n0;
     CU(launch_update(g->dp, ua, s));
+    ++g->launches;
+    g->phase_ran[KNN_PHASE_OFFERS] = true;
+    phase_mark(g, KNN_PHASE_MERGE, s);
     MergeArgs ma{};
     ma.nbr_ids = g->nbr_ids;
     ma.nbr_d2 = g->nbr_d2;
@@ -499,6 +532,9 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     ma.totals = g->totals;
     ma.k = K;
     CU(launch_merge(ma, g->sm_count, s));
+    ++g->launches;
+    g->phase_ran[KNN_PHASE_MERGE] = true;
+    phase_mark(g, KNN_NUM_PHASES, s);
     // a9: publish
     g->n = n0 + m;
     g->inserts += m;
@@ -506,6 +542,7 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
 
     if (out_ids) {
         if (is_device_ptr(out_ids)) {
+            ++g->launches;
             CU(launch_fill_ids(out_ids, n0, m, s));
         } else {
             for (int64_t i = 0; i < m; ++i) out_ids[i] = n0 + i;
@@ -514,6 +551,7 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     if (out_nbrs) {
         const bool dev = is_device_ptr(out_nbrs);
         int64_t *target = dev ? out_nbrs : g->out_ids_dev;
+        ++g->launches;
         CU(launch_lists_to_output(g->nbr_ids + n0 * K, g->nbr_d2 + n0 * K, m, K, target, nullptr, s));
         if (!dev) {
             CU(cudaMemcpyAsync(out_nbrs, g->out_ids_dev, (size_t)m * K * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -533,9 +571,15 @@ KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     g->last_stream = s;
+    phase_begin_call(g);
+    phase_mark(g, KNN_PHASE_STORE, s);
     TRY(append_rows(g, vecs, m, 0, g->qbuf, false, s));
+    g->phase_ran[KNN_PHASE_STORE] = true;
+    phase_mark(g, KNN_PHASE_SEARCH, s);
     const uint64_t *keys = nullptr;
     TRY(run_search(g, g->qbuf, m, k_out, (1ull << 63) + query_id0, s, &keys));
+    phase_mark(g, KNN_PHASE_CROSS, s);
+    for (int ph = KNN_PHASE_CROSS + 1; ph <= KNN_NUM_PHASES; ++ph) phase_mark(g, ph, s);
     bool synced = false;
     TRY(emit_keys(g, keys, m, k_out, k_out, out_ids, out_sims, s, &synced));
     g->queries += m;
@@ -641,6 +685,29 @@ KNN_API knn_status knn_graph_stats(knn_graph *g, knn_stats *out) {
     out->adjacency_reads = (int64_t)t[TOT_ADJ_READS];
     out->offers = (int64_t)t[TOT_OFFERS];
     out->device_bytes = (int64_t)g->bytes;
+    out->kernel_launches = g->launches;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_set_timing(knn_graph *g, int32_t enable) {
+    if (!g) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    DeviceGuard dg(g->device);
+    if (enable && !g->ev[0])
+        for (cudaEvent_t &e : g->ev) CU(cudaEventCreate(&e));
+    g->timing = enable != 0;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_last_timing(knn_graph *g, float *out_ms, int32_t n) {
+    if (!g || !out_ms) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (!g->timing) return fail(KNN_ERR_INVALID_ARG, "timing is off");
+    if (n < 0 || n > KNN_NUM_PHASES) return fail(KNN_ERR_INVALID_ARG, "n outside 0..KNN_NUM_PHASES");
+    DeviceGuard dg(g->device);
+    CU(cudaEventSynchronize(g->ev[KNN_NUM_PHASES]));
+    for (int ph = 0; ph < n; ++ph) {
+        out_ms[ph] = 0.f;
+        if (g->phase_ran[ph]) CU(cudaEventElapsedTime(&out_ms[ph], g->ev[ph], g->ev[ph + 1]));
+    }
     return KNN_OK;
 }
 

@@ -42,8 +42,10 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
 # Every symbol include/knn_graph.h declares.
 EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
             "knn_graph_remove", "knn_graph_get_edges", "knn_graph_last_counters",
-            "knn_graph_stats", "knn_graph_destroy", "knn_exact_graph", "knn_last_error",
-            "knn_version")
+            "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_stats",
+            "knn_graph_destroy", "knn_exact_graph", "knn_last_error", "knn_version")
+
+PHASES = ("store", "search", "rescore", "cross", "offers", "merge")
 
 
 class KnnParams(ctypes.Structure):
@@ -58,7 +60,7 @@ class KnnStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "n", "capacity", "removed", "inserts", "queries", "search_evals", "update_evals",
         "cross_evals", "rescore_evals", "restarts", "moves", "adjacency_reads", "offers",
-        "device_bytes")]
+        "device_bytes", "kernel_launches")]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -84,6 +86,8 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_remove": (I32, [P, P, I64, P]),
         "knn_graph_get_edges": (I32, [P, P, P, I64, ctypes.POINTER(I64), P]),
         "knn_graph_last_counters": (I32, [P, P, I64, P]),
+        "knn_graph_set_timing": (I32, [P, I32]),
+        "knn_graph_last_timing": (I32, [P, ctypes.POINTER(ctypes.c_float), I32]),
         "knn_graph_stats": (I32, [P, ctypes.POINTER(KnnStats)]),
         "knn_graph_destroy": (None, [P]),
         "knn_exact_graph": (I32, [P, I64, I32, I32, P, P, P]),
@@ -191,6 +195,16 @@ def knn_graph_last_counters(g, out, stream=None) -> None:
            "knn_graph_last_counters")
 
 
+def knn_graph_set_timing(g, enable: bool) -> None:
+    _check(lib.knn_graph_set_timing(g, int(bool(enable))), "knn_graph_set_timing")
+
+
+def knn_graph_last_timing(g) -> dict:
+    out = (ctypes.c_float * len(PHASES))()
+    _check(lib.knn_graph_last_timing(g, out, len(PHASES)), "knn_graph_last_timing")
+    return dict(zip(PHASES, list(out)))
+
+
 def knn_graph_stats(g) -> dict:
     st = KnnStats()
     _check(lib.knn_graph_stats(g, ctypes.byref(st)), "knn_graph_stats")
@@ -264,6 +278,12 @@ class Graph:
 
     def stats(self) -> dict:
         return knn_graph_stats(self.handle)
+
+    def set_timing(self, enable: bool = True):
+        knn_graph_set_timing(self.handle, enable)
+
+    def last_timing(self) -> dict:
+        return knn_graph_last_timing(self.handle)
 
     def close(self):
         if self.handle:

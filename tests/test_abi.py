@@ -50,7 +50,7 @@ def test_library_exports_every_declared_symbol(knn):
 
 def test_struct_layouts_match_header(knn):
     assert ctypes.sizeof(knn.KnnParams) == 56
-    assert ctypes.sizeof(knn.KnnStats) == 14 * 8
+    assert ctypes.sizeof(knn.KnnStats) == 15 * 8
 
 
 def _params(knn, **kw):
