@@ -216,6 +216,39 @@ KNN_API void knn_graph_destroy(knn_graph *g);
 KNN_API knn_status knn_exact_graph(const float *X, int64_t n, int32_t dim, int32_t k,
                                    int64_t *out_ids, float *out_sims, void *stream);
 
+/*
+ * The query search of knn_graph_query_batch (FP32 rows, no removed nodes)
+ * over a graph held in the caller's own device buffers, without any device
+ * allocation.  The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory -- a process whose device memory is owned by
+ * another allocator or reserved up front, or a loop that cannot afford the
+ * device-wide synchronisation an allocation may cause -- and that therefore
+ * cannot create a knn_graph.
+ *
+ * rows: [n, dim] float32; dim must be 16, 32, 64, 96, 128 or 256 (rows are
+ * used as they are, without padding).  nbr_ids: [n, k] int32 lists, best
+ * first, -1 for an empty slot.  queries: [m, dim] float32.  out_ids:
+ * [m, k_out] int64; out_sims (nullable): [m, k_out] float32.  Every buffer
+ * must be device memory of the current device; nothing is staged.  Query i
+ * uses restart stream 2^63 + query_id0 + i and budget
+ * max(1, floor(n / speedup)), so it returns exactly what
+ * knn_graph_query_batch returns for the same graph and query id.
+ *
+ * Temporaries live in a 16 MiB array inside the library (every GPU that
+ * loads the library keeps it until the process exits); a call needs about
+ * m * n / 8 bytes of it plus small per-query parts and returns
+ * KNN_ERR_CAPACITY, before any device work, when that exceeds 16 MiB.  The
+ * first call on a device looks up the array's device address (make that
+ * first call before any stream capture).  All calls share the array: calls
+ * that overlap on the GPU race; order them on one stream.  Returns after
+ * enqueueing; outputs are valid once the stream reaches the call.
+ */
+KNN_API knn_status knn_search_noalloc(const float *rows, int64_t n, int32_t dim,
+                                      const int32_t *nbr_ids, int32_t k, const float *queries,
+                                      int64_t m, int32_t k_out, double speedup, double expansion,
+                                      uint64_t seed, uint64_t query_id0, int64_t *out_ids,
+                                      float *out_sims, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 KNN_API const char *knn_last_error(void);
 

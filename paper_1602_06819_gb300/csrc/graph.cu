@@ -96,6 +96,11 @@ static knn_status fail(knn_status st, const char *fmt, ...) {
     return st;
 }
 
+knn_status knn::record_error(knn_status st, const char *msg) {
+    g_last_error = msg;
+    return st;
+}
+
 #define CU(call)                                                                      \
     do {                                                                              \
         cudaError_t e_ = (call);                                                      \

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "knn_graph.h"
+
 namespace knn {
 
 // Per-item counters written by the search and update kernels.
@@ -135,6 +137,9 @@ cudaError_t launch_exact(int dp, const ExactArgs &a, cudaStream_t s);
 // snapshot restore: copy int64 lists (checking every id) and recompute their d2
 cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,
                                  int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s);
+
+// set the calling thread's knn_last_error() message (graph.cu)
+knn_status record_error(knn_status st, const char *msg);
 
 // small helpers (misc.cu)
 cudaError_t launch_append(const float *in, int64_t m, int d, int dp, float *rows_fp32,

@@ -43,7 +43,8 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
 EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
             "knn_graph_remove", "knn_graph_get_edges", "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_stats",
-            "knn_graph_destroy", "knn_exact_graph", "knn_last_error", "knn_version")
+            "knn_graph_destroy", "knn_exact_graph", "knn_search_noalloc", "knn_last_error",
+            "knn_version")
 
 PHASES = ("store", "search", "rescore", "cross", "offers", "merge")
 
@@ -91,6 +92,8 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_stats": (I32, [P, ctypes.POINTER(KnnStats)]),
         "knn_graph_destroy": (None, [P]),
         "knn_exact_graph": (I32, [P, I64, I32, I32, P, P, P]),
+        "knn_search_noalloc": (I32, [P, I64, I32, P, I32, P, I64, I32, ctypes.c_double,
+                                     ctypes.c_double, U64, U64, P, P, P]),
         "knn_last_error": (ctypes.c_char_p, []),
         "knn_version": (ctypes.c_char_p, []),
     }
@@ -221,6 +224,20 @@ def knn_exact_graph(X, k: int, out_ids, out_sims=None, stream=None) -> None:
     _check_dtype(out_sims, "float32", "out_sims")
     _check(lib.knn_exact_graph(_ptr(X), X.shape[0], X.shape[1], k, _ptr(out_ids), _ptr(out_sims),
                                _stream(stream)), "knn_exact_graph")
+
+
+def knn_search_noalloc(rows, nbr_ids, queries, k_out: int, speedup: float, expansion: float,
+                       seed: int, query_id0: int, out_ids, out_sims=None, stream=None) -> None:
+    """Query search over caller-held device buffers; allocates no device memory."""
+    _check_dtype(rows, "float32", "rows")
+    _check_dtype(nbr_ids, "int32", "nbr_ids")
+    _check_dtype(queries, "float32", "queries")
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_sims, "float32", "out_sims")
+    _check(lib.knn_search_noalloc(_ptr(rows), rows.shape[0], rows.shape[1], _ptr(nbr_ids),
+                                  nbr_ids.shape[1], _ptr(queries), queries.shape[0], k_out,
+                                  float(speedup), float(expansion), seed, query_id0, _ptr(out_ids),
+                                  _ptr(out_sims), _stream(stream)), "knn_search_noalloc")
 
 
 def knn_version() -> str:
