@@ -141,8 +141,8 @@ struct RowCfg {
     static constexpr int CPL = NC / G;
     static constexpr int RPP = 32 / G;
     static constexpr int QF = CPL * E;  // query floats held by a lane
-    // passes in flight: about 16 chunk loads per lane, at most 32 rows
-    static constexpr int P_LOADS = 16 / CPL > 1 ? 16 / CPL : 1;
+    // passes in flight: up to 32 chunk loads per lane, at most 32 rows
+    static constexpr int P_LOADS = 32 / CPL > 1 ? 32 / CPL : 1;
     static constexpr int P = P_LOADS < 32 / RPP ? P_LOADS : 32 / RPP;
     static constexpr int ROW_BYTES = STORAGE == ST_FP32 ? DP * 4 : STORAGE == ST_BF16 ? DP * 2 : DP;
     static_assert(DP % 16 == 0, "rows are padded to 16 elements");
@@ -242,6 +242,7 @@ __device__ __forceinline__ float gather_d2(const RowSource &src, uint32_t rid, i
         }
 #pragma unroll
         for (int p = 0; p < C::P; ++p) {
+            if ((p0 + p) * C::RPP >= nrows) break;  // warp-uniform: no rows left
             float acc = 0.0f;
 #pragma unroll
             for (int k = 0; k < C::CPL; ++k) acc = chunk_d2<STORAGE>(buf[p][k], qv + k * C::E, scl[p], acc);

@@ -8,17 +8,26 @@
 // visited set so that no similarity is computed twice, and a budget of
 // B = max(1, floor(n / speedup)) similarity computations.
 //
-// The decisions are sequential, but the row gathers need not be: the
-// similarity of a drawn node does not depend on the search state, so the
-// warp draws up to 32 restart candidates ahead, gathers and reduces their
-// rows together (16-byte coalesced loads, many rows in flight), and then
-// takes the decisions one candidate at a time in draw order.  A candidate
-// that became visited in between (an earlier duplicate in the batch, or a
-// node reached by a climb) is skipped as the sequential search would skip
-// it, at no cost to the budget.  A climb step likewise gathers every
-// unvisited neighbour of the current node at once and then scans them in
-// list order, stopping at the first improvement.  Rows gathered ahead but
-// not reached by the sequential scan are not counted, marked or offered.
+// The decisions are sequential, but neither the row gathers nor most of the
+// decisions need to be taken one at a time:
+//
+// * Restarts.  The similarity of a drawn node does not depend on the search
+//   state, so the warp draws up to 32 unvisited candidates ahead and gathers
+//   their rows together (16-byte coalesced loads, all in flight at once).
+//   Between two accepted restarts the search only counts, marks and offers:
+//   one ballot finds the first candidate the expansion test keeps, and every
+//   candidate before it is committed at once (a discarded restart cannot
+//   change s_max, and the final top list does not depend on the order of the
+//   offers).  Duplicates inside a batch are found with one match instruction;
+//   candidates a climb has visited since the draw are skipped as free redraws.
+// * Climbs.  A step gathers the rows of all neighbours of the current node in
+//   the same round trip as their visited bits; one ballot then finds the
+//   first unvisited neighbour (in list order) that is strictly more similar,
+//   and every unvisited neighbour up to it is committed.
+//
+// Every similarity computation is thus one the sequential search performs:
+// rows gathered ahead but not reached are not counted, marked or offered, and
+// the budget cuts a batch exactly where the sequential search would stop.
 #pragma once
 
 #include "common.cuh"
@@ -28,21 +37,45 @@ namespace knn {
 
 constexpr int SEARCH_WARPS = 4;
 
-__device__ __forceinline__ bool test_bit(const uint32_t *bits, uint32_t i) {
-    return (bits[i >> 5] >> (i & 31)) & 1u;
-}
 __device__ __forceinline__ bool test_bit_ro(const uint32_t *bits, uint32_t i) {
     return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
 }
+// visited bits are set with atomics at L2; read them from L2 too
+__device__ __forceinline__ bool test_bit_l2(const uint32_t *bits, uint32_t i) {
+    return (__ldcg(bits + (i >> 5)) >> (i & 31)) & 1u;
+}
+
+// Lanes whose bit is set in `mask`, keeping only the `count` lowest.
+__device__ __forceinline__ unsigned lowest_bits(unsigned mask, long long count) {
+    if (count >= 32) return mask;
+    const int lane = threadIdx.x & 31;
+    const int rank = __popc(mask & ((1u << lane) - 1u));
+    return __ballot_sync(FULL, ((mask >> lane) & 1u) && rank < count);
+}
+
+// Bits 0 .. i (i < 32).
+__device__ __forceinline__ unsigned upto(int i) { return i >= 31 ? FULL : ((2u << i) - 1u); }
+
+// Offer the keys of the lanes in `lanes` to the warp's top list.  The final
+// list does not depend on the order; lanes go in increasing order.
+template <int T>
+__device__ __forceinline__ void offer_lanes(WarpTop<T> &top, unsigned lanes, uint64_t key) {
+    const int lane = threadIdx.x & 31;
+    unsigned om = __ballot_sync(FULL, ((lanes >> lane) & 1u) && key < top.worst);
+    while (om) {
+        const int l = __ffs(om) - 1;
+        top.offer(shfl_u64(key, l));
+        om &= ~(1u << l);
+        om &= __ballot_sync(FULL, key < top.worst);
+    }
+}
 
 template <int STORAGE, int DP, int T>
-__global__ void __launch_bounds__(SEARCH_WARPS * 32)
+__global__ void __launch_bounds__(SEARCH_WARPS * 32, 2)
 ignns_search_kernel(const SearchArgs a) {
     using C = RowCfg<STORAGE, DP>;
-    constexpr int NB = (C::P * C::RPP) < 32 ? (C::P * C::RPP) : 32;  // restart batch
     __shared__ uint32_t s_id[SEARCH_WARPS][32];
     __shared__ uint64_t s_j[SEARCH_WARPS][32];
-    __shared__ uint32_t s_nb[SEARCH_WARPS][32];
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -50,6 +83,8 @@ ignns_search_kernel(const SearchArgs a) {
     const RowSource src{a.rows, a.row_scale};
     const int nwarps = gridDim.x * SEARCH_WARPS;
     const float INF = __int_as_float(0x7f800000);
+    // each evaluation visits a new node, so evals also counts visited nodes
+    const long long limit = a.budget < a.n_live ? a.budget : a.n_live;
 
     for (int qi = blockIdx.x * SEARCH_WARPS + wib; qi < a.m; qi += nwarps) {
         float qv[C::QF];
@@ -59,30 +94,33 @@ ignns_search_kernel(const SearchArgs a) {
 
         WarpTop<T> top;
         top.init(a.KT);
-        long long evals = 0, nvis = 0, restarts = 0, discarded = 0, moves = 0, adj = 0;
+        long long evals = 0, restarts = 0, discarded = 0, moves = 0, adj = 0;
         unsigned long long draws_used = 0;
         uint64_t j = 0;
-        float d2min = INF;   // s_max = sim_of_d2(d2min); -inf while no node is known
-        float thr = 0.0f;    // s_max / e
-        bool done = a.budget <= 0 || a.n_live <= 0;
+        float d2min = INF;  // s_max = sim_of_d2(d2min); none while d2min is +inf
+        float thr = 0.0f;   // s_max / e
+        bool done = limit <= 0;
 
         while (!done) {
-            // ---- draw the next restart candidates (free redraws skipped)
+            // ---- draw the next restart candidates (free redraws skipped), no
+            // more than the budget can still evaluate
+            const int want = limit - evals < 32 ? (int)(limit - evals) : 32;
             int nc = 0;
-            while (nc < NB && j < a.max_draws && nvis < a.n_live) {
+            __syncwarp();  // marks made so far are visible to the bit reads
+            while (nc < want && j < a.max_draws) {
                 const uint64_t jj = j + (uint64_t)lane;
                 const bool valid = jj < a.max_draws;
                 const uint32_t r = valid ? restart_node(rkey, jj, a.n) : 0u;
-                const bool good = valid && !test_bit_ro(a.removed, r) && !test_bit(vis, r);
+                const bool good = valid && !test_bit_ro(a.removed, r) && !test_bit_l2(vis, r);
                 const unsigned bal = __ballot_sync(FULL, good);
                 const int avail = __popc(bal);
-                const int take = avail < NB - nc ? avail : NB - nc;
+                const int take = avail < want - nc ? avail : want - nc;
                 const int rank = __popc(bal & lt_mask);
                 if (good && rank < take) {
                     s_id[wib][nc + rank] = r;
                     s_j[wib][nc + rank] = jj;
                 }
-                if (take > 0 && take == NB - nc && take < avail) {
+                if (take > 0 && take < avail) {
                     // batch full: resume after the last draw taken
                     const int last = __ffs(__ballot_sync(FULL, good && rank == take - 1)) - 1;
                     j += (uint64_t)last + 1u;
@@ -94,69 +132,78 @@ ignns_search_kernel(const SearchArgs a) {
             }
             __syncwarp();
             if (nc == 0) break;  // nothing left to draw
-            const uint32_t cid = lane < nc ? s_id[wib][lane] : 0u;
+            const uint32_t cid = lane < nc ? s_id[wib][lane] : 0xffffffffu;
             const uint64_t cj = lane < nc ? s_j[wib][lane] : 0ull;
-            const float cd2 = gather_d2<STORAGE, DP>(src, cid, nc, qv);
+            const float cd2 = gather_d2<STORAGE, DP>(src, lane < nc ? cid : 0u, nc, qv);
+            const uint64_t ckey = pack_key(cd2, cid);
+            // an earlier copy of the same node in the batch makes this one a redraw
+            const unsigned same = __match_any_sync(FULL, cid);
+            unsigned skip = __ballot_sync(FULL, lane >= nc || (same & lt_mask) != 0u);
 
-            // ---- decisions in draw order
-            unsigned revisited = 0;  // candidates reached by a climb since the draw
-            for (int c = 0; c < nc; ++c) {
-                if (evals >= a.budget || nvis >= a.n_live) { done = true; break; }
-                const uint32_t r = __shfl_sync(FULL, cid, c);
-                const bool dup = __ballot_sync(FULL, lane < c && cid == r) != 0u;
-                if (dup || ((revisited >> c) & 1u)) continue;  // free redraw
-                const float d2 = __shfl_sync(FULL, cd2, c);
-                ++evals; ++nvis; ++restarts;
-                draws_used = __shfl_sync(FULL, cj, c) + 1ull;
-                if (lane == 0) vis[r >> 5] |= 1u << (r & 31);
-                top.offer(pack_key(d2, r));
-                // expansion test: discard r if sim(q, r) < s_max / e
-                if (a.discard && d2min < INF) {
-                    if (sim_of_d2(d2) < thr) { ++discarded; continue; }
-                }
-                if (d2 < d2min) { d2min = d2; thr = sim_of_d2(d2min) / a.expansion; }
+            // ---- decisions, in draw order
+            int start = 0;
+            while (true) {
+                unsigned ev = ~skip & (FULL << start);
+                if (ev == 0u) break;
+                ev = lowest_bits(ev, limit - evals);
+                // the first candidate the expansion test keeps (all are kept
+                // while no s_max exists)
+                bool keep = false;
+                if ((ev >> lane) & 1u)
+                    keep = !a.discard || !(d2min < INF) || !(sim_of_d2(cd2) < thr);
+                const unsigned kept = __ballot_sync(FULL, keep);
+                const int ai = kept ? __ffs(kept) - 1 : 32;
+                const unsigned evm = ai < 32 ? (ev & upto(ai)) : ev;
+                const int ne = __popc(evm);
+                evals += ne;
+                restarts += ne;
+                discarded += ne - (ai < 32 ? 1 : 0);
+                draws_used = shfl_u64(cj, 31 - __clz(evm)) + 1ull;
+                if ((evm >> lane) & 1u) atomicOr(vis + (cid >> 5), 1u << (cid & 31));
+                offer_lanes(top, evm, ckey);
+                if (ai == 32) break;  // the rest of the batch was discarded
+                const float d2a = __shfl_sync(FULL, cd2, ai);
+                if (d2a < d2min) { d2min = d2a; thr = sim_of_d2(d2min) / a.expansion; }
+                if (evals >= limit) { done = true; break; }
 
-                // ---- eager hill climbing from r
-                uint32_t cur = r;
-                float d2cur = d2;
+                // ---- eager hill climbing from the kept restart
+                uint32_t cur = __shfl_sync(FULL, cid, ai);
+                float d2cur = d2a;
                 while (true) {
                     const int32_t nb = lane < a.k ? __ldg(a.nbr + (size_t)cur * a.k + lane) : -1;
                     ++adj;
+                    const bool valid = nb >= 0 && !test_bit_ro(a.removed, (uint32_t)nb);
                     __syncwarp();
-                    const bool unv = nb >= 0 && !test_bit_ro(a.removed, (uint32_t)nb) &&
-                                     !test_bit(vis, (uint32_t)nb);
-                    const unsigned um = __ballot_sync(FULL, unv);
+                    const bool seen = valid && test_bit_l2(vis, (uint32_t)nb);
+                    const float nd2 = gather_d2<STORAGE, DP>(src, valid ? (uint32_t)nb : 0u, a.k, qv);
+                    unsigned um = __ballot_sync(FULL, valid && !seen);
                     if (um == 0u) break;  // every neighbour visited: local maximum
-                    const int nu = __popc(um);
-                    if (unv) s_nb[wib][__popc(um & lt_mask)] = (uint32_t)nb;
-                    __syncwarp();
-                    const uint32_t nid = lane < nu ? s_nb[wib][lane] : 0u;
-                    const float nd2 = gather_d2<STORAGE, DP>(src, nid, nu, qv);
-                    bool moved = false;
-                    for (int i = 0; i < nu; ++i) {
-                        if (evals >= a.budget) { done = true; break; }
-                        const uint32_t id = __shfl_sync(FULL, nid, i);
-                        const float dd = __shfl_sync(FULL, nd2, i);
-                        ++evals; ++nvis;
-                        if (lane == 0) vis[id >> 5] |= 1u << (id & 31);
-                        top.offer(pack_key(dd, id));
-                        if (dd < d2min) { d2min = dd; thr = sim_of_d2(d2min) / a.expansion; }
-                        if (dd < d2cur) {  // first strict increase of similarity: move
-                            cur = id;
-                            d2cur = dd;
-                            ++moves;
-                            moved = true;
-                            break;
-                        }
-                    }
-                    if (done || !moved) break;
+                    um = lowest_bits(um, limit - evals);
+                    const unsigned better = um & __ballot_sync(FULL, nd2 < d2cur);
+                    const int mi = better ? __ffs(better) - 1 : 32;
+                    const unsigned evc = mi < 32 ? (um & upto(mi)) : um;
+                    evals += __popc(evc);
+                    const bool mine = (evc >> lane) & 1u;
+                    if (mine) atomicOr(vis + ((uint32_t)nb >> 5), 1u << (nb & 31));
+                    offer_lanes(top, evc, pack_key(nd2, (uint32_t)nb));
+                    float mn = mine ? nd2 : INF;
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) mn = fminf(mn, __shfl_xor_sync(FULL, mn, off));
+                    if (mn < d2min) { d2min = mn; thr = sim_of_d2(d2min) / a.expansion; }
+                    if (mi < 32) ++moves;
+                    if (evals >= limit) { done = true; break; }
+                    if (mi == 32) break;  // no unvisited neighbour is more similar
+                    cur = (uint32_t)__shfl_sync(FULL, nb, mi);  // first strict increase: move
+                    d2cur = __shfl_sync(FULL, nd2, mi);
                 }
                 if (done) break;
                 // the climb may have visited candidates drawn earlier
                 __syncwarp();
-                const bool rv = lane > c && lane < nc && test_bit(vis, cid);
-                revisited |= __ballot_sync(FULL, rv);
+                skip |= __ballot_sync(FULL, lane > ai && lane < nc && test_bit_l2(vis, cid));
+                start = ai + 1;
+                if (start >= 32) break;
             }
+            if (evals >= limit) done = true;
         }
 
         // ---- results and counters
