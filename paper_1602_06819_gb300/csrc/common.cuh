@@ -173,6 +173,27 @@ __device__ __forceinline__ void load_query(const float *q, float (&qv)[RowCfg<ST
     }
 }
 
+// Global loads as volatile asm: volatile asm statements keep their program
+// order, so loads placed early are issued early even under register
+// pressure, and the round trips of independent loads overlap.
+__device__ __forceinline__ uint4 ld_nc_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_nc_u32(const void *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+// L2-coherent load (bypasses L1): sees atomics other lanes made at L2
+__device__ __forceinline__ uint32_t ld_cg_u32(const void *p) {
+    uint32_t v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
@@ -216,13 +237,19 @@ __device__ __forceinline__ float chunk_d2(uint4 w, const float *qv, float scale,
     return acc;
 }
 
-// Squared distances of up to 32 rows.  Lane c (c < nrows) holds row id
-// `rid`; on return lane c holds the squared distance of its row (other lanes
-// return +inf).  All 32 lanes must call.
-template <int STORAGE, int DP>
+// The row layout with at most MAX_ROWS rows in flight.
+template <int STORAGE, int DP, int MAX_ROWS>
+struct GatherCfg : RowCfg<STORAGE, DP> {
+    using C0 = RowCfg<STORAGE, DP>;
+    static constexpr int P = C0::P * C0::RPP <= MAX_ROWS ? C0::P
+                             : (MAX_ROWS / C0::RPP > 0 ? MAX_ROWS / C0::RPP : 1);
+};
+
+// MAX_ROWS bounds the rows in flight at once (and the registers they take).
+template <int STORAGE, int DP, int MAX_ROWS = 32>
 __device__ __forceinline__ float gather_d2(const RowSource &src, uint32_t rid, int nrows,
                                            const float (&qv)[RowCfg<STORAGE, DP>::QF]) {
-    using C = RowCfg<STORAGE, DP>;
+    using C = GatherCfg<STORAGE, DP, MAX_ROWS>;
     const int lane = threadIdx.x & 31;
     const int gl = lane / C::G, gi = lane % C::G;
     float result = __int_as_float(0x7f800000);
@@ -236,9 +263,12 @@ __device__ __forceinline__ float gather_d2(const RowSource &src, uint32_t rid, i
             const bool act = c < nrows;
             const uint4 *base = reinterpret_cast<const uint4 *>(src.rows + (size_t)row * C::ROW_BYTES);
 #pragma unroll
-            for (int k = 0; k < C::CPL; ++k)
-                buf[p][k] = act ? __ldg(base + gi + k * C::G) : make_uint4(0, 0, 0, 0);
-            scl[p] = (STORAGE == ST_FP8 && act) ? __ldg(src.scale + row) : 1.0f;
+            for (int k = 0; k < C::CPL; ++k) {
+                buf[p][k] = make_uint4(0, 0, 0, 0);
+                if (act) buf[p][k] = ld_nc_v4(base + gi + k * C::G);
+            }
+            scl[p] = 1.0f;
+            if (STORAGE == ST_FP8 && act) scl[p] = __uint_as_float(ld_nc_u32(src.scale + row));
         }
 #pragma unroll
         for (int p = 0; p < C::P; ++p) {

@@ -209,7 +209,8 @@ static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int 
                              uint64_t stream_base, cudaStream_t s, const uint64_t **keys_out) {
     const bool screening = g->p.storage != KNN_STORAGE_FP32;
     const int KT = screening ? g->p.rescore_mult * k_out : k_out;
-    CU(cudaMemsetAsync(g->visited, 0, (size_t)m * g->vwords * sizeof(uint32_t), s));
+    if (!search_visited_on_chip((uint32_t)g->n))
+        CU(cudaMemsetAsync(g->visited, 0, (size_t)m * g->vwords * sizeof(uint32_t), s));
     SearchArgs a{};
     a.rows = searched_rows(g);
     a.row_scale = g->scale;

@@ -129,6 +129,9 @@ bool supported_dp(int dp);
 int padded_dim(int d);  // smallest supported DP >= d, or -1
 
 cudaError_t launch_search(int storage, int dp, const SearchArgs &a, cudaStream_t s);
+// true when the search keeps visited sets in shared memory for a graph of n
+// nodes (the global bitsets are then not read and need no clearing)
+bool search_visited_on_chip(uint32_t n);
 cudaError_t launch_rescore(int dp, const RescoreArgs &a, cudaStream_t s);
 cudaError_t launch_cross(int dp, const CrossArgs &a, cudaStream_t s);
 cudaError_t launch_update(int dp, const UpdateArgs &a, cudaStream_t s);

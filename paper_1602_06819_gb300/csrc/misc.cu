@@ -20,6 +20,11 @@ int padded_dim(int d) {
     return -1;
 }
 
+bool search_visited_on_chip(uint32_t n) {
+    // the same rule as the search launcher: 4 warps' bitsets within 110 KiB
+    return (size_t)4 * ((n + 31) / 32) * sizeof(uint32_t) <= (size_t)110 * 1024;
+}
+
 cudaError_t launch_search(int storage, int dp, const SearchArgs &a, cudaStream_t s) {
     switch (storage) {
         case ST_FP32: return launch_search_fp32(dp, a, s);

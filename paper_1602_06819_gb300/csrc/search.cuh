@@ -25,6 +25,11 @@
 //   first unvisited neighbour (in list order) that is strictly more similar,
 //   and every unvisited neighbour up to it is committed.
 //
+// Visited sets.  A query's bitset lives in shared memory when the bitsets of
+// a block's warps fit two blocks on an SM (about 220,000 nodes); marks are
+// then shared-memory atomics and tests cost a few cycles.  Larger graphs keep
+// the bitset in global memory (L2 atomics, L2 reads).
+//
 // Every similarity computation is thus one the sequential search performs:
 // rows gathered ahead but not reached are not counted, marked or offered, and
 // the budget cuts a batch exactly where the sequential search would stop.
@@ -38,11 +43,26 @@ namespace knn {
 constexpr int SEARCH_WARPS = 4;
 
 __device__ __forceinline__ bool test_bit_ro(const uint32_t *bits, uint32_t i) {
-    return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
+    return (ld_nc_u32(bits + (i >> 5)) >> (i & 31)) & 1u;
 }
-// visited bits are set with atomics at L2; read them from L2 too
-__device__ __forceinline__ bool test_bit_l2(const uint32_t *bits, uint32_t i) {
-    return (__ldcg(bits + (i >> 5)) >> (i & 31)) & 1u;
+
+// A query's visited set: a bitset in shared memory or in global memory.
+template <bool SMEM>
+struct Visited {
+    uint32_t *bits;
+    __device__ __forceinline__ bool test(uint32_t i) const {
+        if constexpr (SMEM) return (bits[i >> 5] >> (i & 31)) & 1u;
+        // global bits are set with atomics at L2; read them from L2 too
+        return (ld_cg_u32(bits + (i >> 5)) >> (i & 31)) & 1u;
+    }
+    __device__ __forceinline__ void mark(uint32_t i) const { atomicOr(bits + (i >> 5), 1u << (i & 31)); }
+};
+
+// Shared memory a block may use for visited sets (two blocks per SM); the
+// rule is mirrored by search_visited_on_chip().
+constexpr size_t SEARCH_SMEM_VIS_MAX = 110 * 1024;
+__host__ __device__ constexpr size_t search_smem_bytes(uint32_t n) {
+    return (size_t)SEARCH_WARPS * ((n + 31) / 32) * sizeof(uint32_t);
 }
 
 // Lanes whose bit is set in `mask`, keeping only the `count` lowest.
@@ -70,10 +90,11 @@ __device__ __forceinline__ void offer_lanes(WarpTop<T> &top, unsigned lanes, uin
     }
 }
 
-template <int STORAGE, int DP, int T>
+template <int STORAGE, int DP, int T, bool SMEM_VIS>
 __global__ void __launch_bounds__(SEARCH_WARPS * 32, 2)
 ignns_search_kernel(const SearchArgs a) {
     using C = RowCfg<STORAGE, DP>;
+    extern __shared__ uint32_t s_visited[];  // SMEM_VIS: one bitset per warp
     __shared__ uint32_t s_id[SEARCH_WARPS][32];
     __shared__ uint64_t s_j[SEARCH_WARPS][32];
 
@@ -89,7 +110,15 @@ ignns_search_kernel(const SearchArgs a) {
     for (int qi = blockIdx.x * SEARCH_WARPS + wib; qi < a.m; qi += nwarps) {
         float qv[C::QF];
         load_query<STORAGE, DP>(a.queries + (size_t)qi * a.q_stride, qv);
-        uint32_t *vis = a.visited + (size_t)qi * a.vwords;
+        Visited<SMEM_VIS> vis;
+        if constexpr (SMEM_VIS) {
+            const uint32_t words = (a.n + 31) / 32;
+            vis.bits = s_visited + (size_t)wib * words;
+            for (uint32_t w = lane; w < words; w += 32) vis.bits[w] = 0u;
+            __syncwarp();
+        } else {
+            vis.bits = a.visited + (size_t)qi * a.vwords;
+        }
         const uint64_t rkey = restart_key(a.seed, a.stream_base + (uint64_t)qi);
 
         WarpTop<T> top;
@@ -111,7 +140,7 @@ ignns_search_kernel(const SearchArgs a) {
                 const uint64_t jj = j + (uint64_t)lane;
                 const bool valid = jj < a.max_draws;
                 const uint32_t r = valid ? restart_node(rkey, jj, a.n) : 0u;
-                const bool good = valid && !test_bit_ro(a.removed, r) && !test_bit_l2(vis, r);
+                const bool good = valid && !test_bit_ro(a.removed, r) && !vis.test(r);
                 const unsigned bal = __ballot_sync(FULL, good);
                 const int avail = __popc(bal);
                 const int take = avail < want - nc ? avail : want - nc;
@@ -159,7 +188,7 @@ ignns_search_kernel(const SearchArgs a) {
                 restarts += ne;
                 discarded += ne - (ai < 32 ? 1 : 0);
                 draws_used = shfl_u64(cj, 31 - __clz(evm)) + 1ull;
-                if ((evm >> lane) & 1u) atomicOr(vis + (cid >> 5), 1u << (cid & 31));
+                if ((evm >> lane) & 1u) vis.mark(cid);
                 offer_lanes(top, evm, ckey);
                 if (ai == 32) break;  // the rest of the batch was discarded
                 const float d2a = __shfl_sync(FULL, cd2, ai);
@@ -170,11 +199,11 @@ ignns_search_kernel(const SearchArgs a) {
                 uint32_t cur = __shfl_sync(FULL, cid, ai);
                 float d2cur = d2a;
                 while (true) {
-                    const int32_t nb = lane < a.k ? __ldg(a.nbr + (size_t)cur * a.k + lane) : -1;
+                    const int32_t nb = lane < a.k ? (int32_t)ld_nc_u32(a.nbr + (size_t)cur * a.k + lane) : -1;
                     ++adj;
                     const bool valid = nb >= 0 && !test_bit_ro(a.removed, (uint32_t)nb);
                     __syncwarp();
-                    const bool seen = valid && test_bit_l2(vis, (uint32_t)nb);
+                    const bool seen = valid && vis.test((uint32_t)nb);
                     const float nd2 = gather_d2<STORAGE, DP>(src, valid ? (uint32_t)nb : 0u, a.k, qv);
                     unsigned um = __ballot_sync(FULL, valid && !seen);
                     if (um == 0u) break;  // every neighbour visited: local maximum
@@ -184,7 +213,7 @@ ignns_search_kernel(const SearchArgs a) {
                     const unsigned evc = mi < 32 ? (um & upto(mi)) : um;
                     evals += __popc(evc);
                     const bool mine = (evc >> lane) & 1u;
-                    if (mine) atomicOr(vis + ((uint32_t)nb >> 5), 1u << (nb & 31));
+                    if (mine) vis.mark((uint32_t)nb);
                     offer_lanes(top, evc, pack_key(nd2, (uint32_t)nb));
                     float mn = mine ? nd2 : INF;
 #pragma unroll
@@ -199,7 +228,7 @@ ignns_search_kernel(const SearchArgs a) {
                 if (done) break;
                 // the climb may have visited candidates drawn earlier
                 __syncwarp();
-                skip |= __ballot_sync(FULL, lane > ai && lane < nc && test_bit_l2(vis, cid));
+                skip |= __ballot_sync(FULL, lane > ai && lane < nc && vis.test(cid));
                 start = ai + 1;
                 if (start >= 32) break;
             }
@@ -233,18 +262,28 @@ ignns_search_kernel(const SearchArgs a) {
     }
 }
 
+template <int ST, int DPV, int T>
+static cudaError_t launch_search_t(const SearchArgs &a, cudaStream_t s) {
+    const int grid = (a.m + SEARCH_WARPS - 1) / SEARCH_WARPS;
+    const size_t smem = search_smem_bytes(a.n);
+    if (smem <= SEARCH_SMEM_VIS_MAX) {
+        cudaError_t e = cudaFuncSetAttribute(ignns_search_kernel<ST, DPV, T, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ignns_search_kernel<ST, DPV, T, true><<<grid, SEARCH_WARPS * 32, smem, s>>>(a);
+    } else {
+        ignns_search_kernel<ST, DPV, T, false><<<grid, SEARCH_WARPS * 32, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 #define KNN_SEARCH_CASE(ST, DPV)                                                          \
     case DPV:                                                                             \
-        if (a.KT <= 32)                                                                   \
-            ignns_search_kernel<ST, DPV, 1><<<grid, SEARCH_WARPS * 32, 0, s>>>(a);        \
-        else                                                                              \
-            ignns_search_kernel<ST, DPV, 4><<<grid, SEARCH_WARPS * 32, 0, s>>>(a);        \
-        break;
+        return a.KT <= 32 ? launch_search_t<ST, DPV, 1>(a, s) : launch_search_t<ST, DPV, 4>(a, s);
 
 #define KNN_DEFINE_SEARCH_LAUNCHER(NAME, ST)                                              \
     cudaError_t NAME(int dp, const SearchArgs &a, cudaStream_t s) {                       \
         if (a.m <= 0) return cudaSuccess;                                                 \
-        const int grid = (a.m + SEARCH_WARPS - 1) / SEARCH_WARPS;                         \
         switch (dp) {                                                                     \
             KNN_SEARCH_CASE(ST, 16)                                                       \
             KNN_SEARCH_CASE(ST, 32)                                                       \
@@ -255,7 +294,6 @@ ignns_search_kernel(const SearchArgs a) {
             default:                                                                      \
                 return cudaErrorInvalidValue;                                             \
         }                                                                                 \
-        return cudaGetLastError();                                                        \
     }
 
 }  // namespace knn
