@@ -237,6 +237,59 @@ __device__ __forceinline__ float chunk_d2(uint4 w, const float *qv, float scale,
     return acc;
 }
 
+// Row gathers split in two: issue() starts the loads of up to ROWS rows
+// (lane c < nrows holds row id rid) and reduce() waits for them, leaving the
+// squared distance of row c in lane c.  Work placed between the two calls
+// overlaps with the loads.
+template <int STORAGE, int DP>
+struct RowGather {
+    // at most 32 16-byte chunks per lane (128 registers) stay in flight
+    using C0 = RowCfg<STORAGE, DP>;
+    struct C : C0 {
+        static constexpr int P = C0::P * C0::CPL <= 32 ? C0::P : (32 / C0::CPL > 0 ? 32 / C0::CPL : 1);
+    };
+    static constexpr int ROWS = C::P * C::RPP < 32 ? C::P * C::RPP : 32;
+    uint4 buf[C::P][C::CPL];
+    float scl[C::P];
+
+    __device__ __forceinline__ void issue(const RowSource &src, uint32_t rid, int nrows) {
+        const int lane = threadIdx.x & 31;
+        const int gl = lane / C::G, gi = lane % C::G;
+#pragma unroll
+        for (int p = 0; p < C::P; ++p) {
+            const int c = p * C::RPP + gl;
+            const uint32_t row = __shfl_sync(FULL, rid, c & 31);
+            const bool act = c < nrows;
+            const uint4 *base = reinterpret_cast<const uint4 *>(src.rows + (size_t)row * C::ROW_BYTES);
+#pragma unroll
+            for (int k = 0; k < C::CPL; ++k) {
+                buf[p][k] = make_uint4(0, 0, 0, 0);
+                if (act) buf[p][k] = ld_nc_v4(base + gi + k * C::G);
+            }
+            scl[p] = 1.0f;
+            if (STORAGE == ST_FP8 && act) scl[p] = __uint_as_float(ld_nc_u32(src.scale + row));
+        }
+    }
+
+    __device__ __forceinline__ float reduce(int nrows, const float (&qv)[C::QF]) const {
+        const int lane = threadIdx.x & 31;
+        float result = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int p = 0; p < C::P; ++p) {
+            if (p * C::RPP >= nrows) break;  // warp-uniform: no rows left
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < C::CPL; ++k) acc = chunk_d2<STORAGE>(buf[p][k], qv + k * C::E, scl[p], acc);
+#pragma unroll
+            for (int off = C::G / 2; off >= 1; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+            const int c = lane - p * C::RPP;
+            const float got = __shfl_sync(FULL, acc, ((lane % C::RPP) * C::G) & 31);
+            if (c >= 0 && c < C::RPP && lane < nrows) result = got;
+        }
+        return result;
+    }
+};
+
 // The row layout with at most MAX_ROWS rows in flight.
 template <int STORAGE, int DP, int MAX_ROWS>
 struct GatherCfg : RowCfg<STORAGE, DP> {

@@ -66,7 +66,7 @@ __host__ __device__ constexpr size_t search_smem_bytes(uint32_t n) {
 }
 
 // Lanes whose bit is set in `mask`, keeping only the `count` lowest.
-__device__ __forceinline__ unsigned lowest_bits(unsigned mask, long long count) {
+__device__ __forceinline__ unsigned lowest_bits(unsigned mask, int count) {
     if (count >= 32) return mask;
     const int lane = threadIdx.x & 31;
     const int rank = __popc(mask & ((1u << lane) - 1u));
@@ -94,6 +94,7 @@ template <int STORAGE, int DP, int T, bool SMEM_VIS>
 __global__ void __launch_bounds__(SEARCH_WARPS * 32, 2)
 ignns_search_kernel(const SearchArgs a) {
     using C = RowCfg<STORAGE, DP>;
+    constexpr int NB = RowGather<STORAGE, DP>::ROWS;  // restart candidates per batch
     extern __shared__ uint32_t s_visited[];  // SMEM_VIS: one bitset per warp
     __shared__ uint32_t s_id[SEARCH_WARPS][32];
     __shared__ uint64_t s_j[SEARCH_WARPS][32];
@@ -105,7 +106,7 @@ ignns_search_kernel(const SearchArgs a) {
     const int nwarps = gridDim.x * SEARCH_WARPS;
     const float INF = __int_as_float(0x7f800000);
     // each evaluation visits a new node, so evals also counts visited nodes
-    const long long limit = a.budget < a.n_live ? a.budget : a.n_live;
+    const int limit = (int)(a.budget < a.n_live ? a.budget : a.n_live);
 
     for (int qi = blockIdx.x * SEARCH_WARPS + wib; qi < a.m; qi += nwarps) {
         float qv[C::QF];
@@ -123,17 +124,16 @@ ignns_search_kernel(const SearchArgs a) {
 
         WarpTop<T> top;
         top.init(a.KT);
-        long long evals = 0, restarts = 0, discarded = 0, moves = 0, adj = 0;
+        int evals = 0, restarts = 0, discarded = 0, moves = 0, adj = 0;  // budgets are < 2^31
         unsigned long long draws_used = 0;
         uint64_t j = 0;
         float d2min = INF;  // s_max = sim_of_d2(d2min); none while d2min is +inf
         float thr = 0.0f;   // s_max / e
         bool done = limit <= 0;
 
-        while (!done) {
-            // ---- draw the next restart candidates (free redraws skipped), no
-            // more than the budget can still evaluate
-            const int want = limit - evals < 32 ? (int)(limit - evals) : 32;
+        // Draw up to `want` candidates after draw j, skipping nodes visited or
+        // removed (free redraws); lane c < count receives candidate c.
+        auto draw = [&](int want, uint32_t &id, uint64_t &dj) -> int {
             int nc = 0;
             __syncwarp();  // marks made so far are visible to the bit reads
             while (nc < want && j < a.max_draws) {
@@ -160,26 +160,49 @@ ignns_search_kernel(const SearchArgs a) {
                 nc += take;
             }
             __syncwarp();
-            if (nc == 0) break;  // nothing left to draw
-            const uint32_t cid = lane < nc ? s_id[wib][lane] : 0xffffffffu;
-            const uint64_t cj = lane < nc ? s_j[wib][lane] : 0ull;
-            const float cd2 = gather_d2<STORAGE, DP>(src, lane < nc ? cid : 0u, nc, qv);
-            const uint64_t ckey = pack_key(cd2, cid);
-            // an earlier copy of the same node in the batch makes this one a redraw
-            const unsigned same = __match_any_sync(FULL, cid);
-            unsigned skip = __ballot_sync(FULL, lane >= nc || (same & lt_mask) != 0u);
+            id = lane < nc ? s_id[wib][lane] : 0xffffffffu;
+            dj = lane < nc ? s_j[wib][lane] : 0ull;
+            return nc;
+        };
+        auto cap = [&](int room) -> int { return room < NB ? room : NB; };
 
-            // ---- decisions, in draw order
-            int start = 0;
-            while (true) {
+        // Batch A is decided while the rows of the next batch B load.
+        RowGather<STORAGE, DP> G;
+        uint32_t aid = 0xffffffffu;
+        uint64_t aj = 0;
+        int an = done ? 0 : draw(cap(limit), aid, aj);
+        float ad2 = __int_as_float(0x7f800000);
+        if (an > 0) {
+            G.issue(src, lane < an ? aid : 0u, an);
+            ad2 = G.reduce(an, qv);
+        }
+        while (an > 0) {
+            // ---- draw B (filtered by the marks so far) and start its loads
+            uint32_t bid = 0xffffffffu;
+            uint64_t bj = 0;
+            const int room = limit - evals - an;
+            int bn = room > 0 ? draw(cap(room), bid, bj) : 0;
+            // issue and reduce are paired unconditionally (no loads for bn = 0),
+            // so the row buffer is visibly dead after the reduce
+            G.issue(src, lane < bn ? bid : 0u, bn);
+
+            // ---- decide A, in draw order.  A was filtered before the batch
+            // before it was decided: re-test its candidates; an earlier copy of
+            // the same node in A makes a candidate a redraw.
+            const uint64_t akey = pack_key(ad2, aid);
+            const unsigned same = __match_any_sync(FULL, aid);
+            unsigned skip = __ballot_sync(FULL, lane >= an || (same & lt_mask) != 0u || vis.test(aid));
+            // Commit the candidates from `start` up to the first one the
+            // expansion test keeps (all are kept while no s_max exists);
+            // returns that candidate, or 32 when every candidate left was
+            // discarded or skipped.
+            auto segment = [&](int start) -> int {
                 unsigned ev = ~skip & (FULL << start);
-                if (ev == 0u) break;
+                if (ev == 0u) return 32;
                 ev = lowest_bits(ev, limit - evals);
-                // the first candidate the expansion test keeps (all are kept
-                // while no s_max exists)
                 bool keep = false;
                 if ((ev >> lane) & 1u)
-                    keep = !a.discard || !(d2min < INF) || !(sim_of_d2(cd2) < thr);
+                    keep = !a.discard || !(d2min < INF) || !(sim_of_d2(ad2) < thr);
                 const unsigned kept = __ballot_sync(FULL, keep);
                 const int ai = kept ? __ffs(kept) - 1 : 32;
                 const unsigned evm = ai < 32 ? (ev & upto(ai)) : ev;
@@ -187,16 +210,22 @@ ignns_search_kernel(const SearchArgs a) {
                 evals += ne;
                 restarts += ne;
                 discarded += ne - (ai < 32 ? 1 : 0);
-                draws_used = shfl_u64(cj, 31 - __clz(evm)) + 1ull;
-                if ((evm >> lane) & 1u) vis.mark(cid);
-                offer_lanes(top, evm, ckey);
-                if (ai == 32) break;  // the rest of the batch was discarded
-                const float d2a = __shfl_sync(FULL, cd2, ai);
+                draws_used = shfl_u64(aj, 31 - __clz(evm)) + 1ull;
+                if ((evm >> lane) & 1u) vis.mark(aid);
+                offer_lanes(top, evm, akey);
+                return ai;
+            };
+            int ai = segment(0);
+            // B's distances, before any climb (one row buffer is live at a time)
+            const float bd2 = G.reduce(bn, qv);
+
+            while (ai < 32) {
+                const float d2a = __shfl_sync(FULL, ad2, ai);
                 if (d2a < d2min) { d2min = d2a; thr = sim_of_d2(d2min) / a.expansion; }
                 if (evals >= limit) { done = true; break; }
 
                 // ---- eager hill climbing from the kept restart
-                uint32_t cur = __shfl_sync(FULL, cid, ai);
+                uint32_t cur = __shfl_sync(FULL, aid, ai);
                 float d2cur = d2a;
                 while (true) {
                     const int32_t nb = lane < a.k ? (int32_t)ld_nc_u32(a.nbr + (size_t)cur * a.k + lane) : -1;
@@ -228,11 +257,25 @@ ignns_search_kernel(const SearchArgs a) {
                 if (done) break;
                 // the climb may have visited candidates drawn earlier
                 __syncwarp();
-                skip |= __ballot_sync(FULL, lane > ai && lane < nc && vis.test(cid));
-                start = ai + 1;
-                if (start >= 32) break;
+                skip |= __ballot_sync(FULL, lane > ai && lane < an && vis.test(aid));
+                ai = ai + 1 < 32 ? segment(ai + 1) : 32;
             }
             if (evals >= limit) done = true;
+            if (done) break;
+            if (bn == 0) {  // B was not drawn ahead (the budget looked spent)
+                bn = draw(cap(limit - evals), bid, bj);
+                if (bn == 0) break;
+                G.issue(src, lane < bn ? bid : 0u, bn);
+                aid = bid;
+                aj = bj;
+                an = bn;
+                ad2 = G.reduce(bn, qv);
+                continue;
+            }
+            aid = bid;
+            aj = bj;
+            an = bn;
+            ad2 = bd2;
         }
 
         // ---- results and counters
