@@ -65,7 +65,7 @@ typedef enum knn_storage {
 typedef struct knn_params {
     int32_t dim;          /* vector dimension d, 1 .. 256                         */
     int32_t k;            /* neighbours per node, 1 .. 32 (Sec. 1)                */
-    int32_t depth;        /* Update DEPTH (Algorithm 2), 1 or 2                   */
+    int32_t depth;        /* Update DEPTH (Algorithm 2), 1 .. 5                   */
     int32_t storage;      /* knn_storage of the searched copy                     */
     double speedup;       /* iGNNS budget: B = max(1, floor(n / speedup))
                              similarities per search (Sec. 3); > 0                */

@@ -33,7 +33,7 @@ struct knn_graph {
     int sm_count = 0;
     int dp = 0;
     int KT = 0;            // candidates kept by an insert's search
-    int hash_size = 0;
+    int64_t frontier_cap = 0;  // Update level entries kept per new point
     int64_t n = 0;
     int64_t n_removed = 0;
     int64_t inserts = 0, queries = 0;
@@ -61,6 +61,7 @@ struct knn_graph {
     uint64_t *offer_key = nullptr;
     int32_t *offer_next = nullptr;
     int32_t *touched = nullptr;
+    int32_t *frontier = nullptr;
     unsigned *small = nullptr;  // [0] offers, [1] touched, [2] error flags
     unsigned long long *totals = nullptr;
     int64_t *out_ids_dev = nullptr;
@@ -135,12 +136,6 @@ static int64_t budget_of(int64_t n, double speedup) {
     // B = max(1, floor(n / speedup)), the iGNNS similarity budget (Sec. 3)
     double b = std::floor((double)n / speedup);
     return b < 1.0 ? 1 : (int64_t)b;
-}
-
-static int next_pow2(int v) {
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
 }
 
 template <class T>
@@ -297,7 +292,7 @@ KNN_API const char *knn_version(void) { return "knn_graph 0.1 (sm_103a)"; }
 static knn_status validate_params(const knn_params &p, int64_t n_init) {
     if (p.dim < 1 || p.dim > 256) return fail(KNN_ERR_UNSUPPORTED, "dim %d outside 1..256", p.dim);
     if (p.k < 1 || p.k > 32) return fail(KNN_ERR_UNSUPPORTED, "k %d outside 1..32", p.k);
-    if (p.depth < 1 || p.depth > 2) return fail(KNN_ERR_UNSUPPORTED, "depth %d outside 1..2", p.depth);
+    if (p.depth < 1 || p.depth > 5) return fail(KNN_ERR_UNSUPPORTED, "depth %d outside 1..5", p.depth);
     if (p.storage < 0 || p.storage > 2) return fail(KNN_ERR_INVALID_ARG, "bad storage %d", p.storage);
     if (!(p.speedup > 0.0) || !std::isfinite(p.speedup))
         return fail(KNN_ERR_INVALID_ARG, "speedup must be finite and > 0");
@@ -325,15 +320,24 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
     }
     g->dp = padded_dim(p.dim);
     g->KT = g->p.rescore_mult * p.k;
-    g->hash_size = next_pow2(2 * (1 + p.k + p.k * p.k));
     g->vwords = (p.capacity + 31) / 32;
     const int64_t C = p.capacity, M = p.max_batch, K = p.k, DP = g->dp;
-    g->offer_cap = (unsigned)(M * (K + K * K));
+    // Update levels of one new point: k + k^2 + ... + k^DEPTH entries at
+    // most, and never more than k plus the nodes of the graph
+    int64_t levels = 0, pw = 1;
+    for (int t = 1; t <= p.depth; ++t) {
+        pw = std::min<int64_t>(pw * K, C + K);
+        levels = std::min<int64_t>(levels + pw, C + K);
+    }
+    g->frontier_cap = levels;
+    if ((double)M * (double)(K + levels) >= 4.0e9)
+        return fail(KNN_ERR_UNSUPPORTED, "max_batch * (k + Update levels) exceeds 2^32 candidates");
+    g->offer_cap = (unsigned)(M * (K + levels));
 
     size_t need = (size_t)C * DP * 4 + (size_t)C * K * 8 + (size_t)g->vwords * 4 + (size_t)C * 4 +
                   (size_t)M * g->vwords * 4 + (size_t)M * DP * 4 + (size_t)M * p.dim * 4 +
                   (size_t)M * g->KT * 8 + (size_t)M * K * 8 + (size_t)M * NCTR * 8 +
-                  (size_t)g->offer_cap * 16 + (size_t)M * K * 12;
+                  (size_t)g->offer_cap * 16 + (size_t)M * K * 12 + (size_t)M * levels * 4;
     if (p.storage == KNN_STORAGE_BF16) need += (size_t)C * DP * 2;
     if (p.storage == KNN_STORAGE_FP8_E4M3) need += (size_t)C * DP + (size_t)C * 4;
     size_t free_b = 0, total_b = 0;
@@ -366,6 +370,7 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
     ALLOC(offer_key, g->offer_cap)
     ALLOC(offer_next, g->offer_cap)
     ALLOC(touched, g->offer_cap)
+    ALLOC(frontier, M * levels)
     ALLOC(small, 4)
     ALLOC(totals, NTOT)
     ALLOC(out_ids_dev, M * K)
@@ -520,8 +525,13 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     ua.m = (int32_t)m;
     ua.k = K;
     ua.depth = g->p.depth;
-    ua.hash_size = g->hash_size;
+    ua.frontier = g->frontier;
+    ua.frontier_cap = g->frontier_cap;
+    ua.seen = g->visited;
+    ua.seen_words = (n0 + m + 31) / 32;
     ua.n = (uint32_t)n0;
+    if (ua.depth >= 2 && !update_seen_on_chip(ua.seen_words))
+        CU(cudaMemsetAsync(g->visited, 0, (size_t)m * ua.seen_words * sizeof(uint32_t), s));
     CU(launch_update(g->dp, ua, s));
     ++g->launches;
     g->phase_ran[KNN_PHASE_OFFERS] = true;

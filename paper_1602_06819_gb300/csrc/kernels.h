@@ -98,7 +98,11 @@ struct UpdateArgs {
     unsigned *error_flags;
     long long *counters;         // [m][NCTR]
     unsigned long long *totals;
-    int32_t m, k, depth, hash_size;
+    int32_t *frontier;           // [m][frontier_cap] nodes of the Update levels
+    int64_t frontier_cap;        // min(nodes, k + k^2 + ... + k^DEPTH)
+    uint32_t *seen;              // [m][seen_words] global seen bitsets (zeroed), if not on chip
+    int64_t seen_words;          // ceil((n + m) / 32)
+    int32_t m, k, depth;
     uint32_t n;                  // graph size before the batch
 };
 
@@ -136,6 +140,8 @@ cudaError_t launch_rescore(int dp, const RescoreArgs &a, cudaStream_t s);
 cudaError_t launch_cross(int dp, const CrossArgs &a, cudaStream_t s);
 cudaError_t launch_update(int dp, const UpdateArgs &a, cudaStream_t s);
 cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t s);
+// true when Update keeps its seen bitsets (seen_words words each) on chip
+bool update_seen_on_chip(int64_t seen_words);
 cudaError_t launch_exact(int dp, const ExactArgs &a, cudaStream_t s);
 // snapshot restore: copy int64 lists (checking every id) and recompute their d2
 cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,

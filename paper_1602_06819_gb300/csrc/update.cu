@@ -128,28 +128,20 @@ __device__ __forceinline__ void push_offers(const UpdateArgs &a, bool has, uint3
     }
 }
 
-// Insert into the warp's open-addressing set; true if `v` was not there.
-__device__ __forceinline__ bool hash_insert(uint32_t *table, int size, uint32_t v) {
-    uint32_t h = (v * 0x9E3779B1u) & (uint32_t)(size - 1);
-    for (int probe = 0; probe < size; ++probe) {
-        const uint32_t old = atomicCAS(table + h, 0xffffffffu, v);
-        if (old == 0xffffffffu) return true;
-        if (old == v) return false;
-        h = (h + 1u) & (uint32_t)(size - 1);
-    }
-    return false;  // full: cannot happen, the table holds twice the ids offered
-}
+// Rows of Update levels: while the "seen" bitsets of a block's warps fit
+// in 110 KiB of shared memory they live there, otherwise in global memory
+// (cleared by the host before the launch).
+constexpr size_t UPD_SMEM_SEEN_MAX = 110 * 1024;
 
-template <int DP>
+template <int DP, bool SMEM_SEEN>
 __global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const UpdateArgs a) {
     using C = RowCfg<ST_FP32, DP>;
-    extern __shared__ uint32_t smem[];
+    extern __shared__ uint32_t smem_seen[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int i = blockIdx.x * UPD_WARPS + wib;
     if (i >= a.m) return;
-    uint32_t *table = smem + (size_t)wib * (a.hash_size + a.k * a.k);
-    uint32_t *frontier = table + a.hash_size;
 
     const uint32_t new_id = a.n + (uint32_t)i;
     const RowSource src{reinterpret_cast<const uint8_t *>(a.rows), nullptr};
@@ -168,42 +160,71 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const Upd
         push_offers(a, has, (uint32_t)lid, key);
     }
 
-    long long upd_evals = 0;
+    int upd_evals = 0;
     if (a.depth >= 2) {
-        for (int t = lane; t < a.hash_size; t += 32) table[t] = 0xffffffffu;
-        __syncwarp();
-        if (lane == 0) hash_insert(table, a.hash_size, new_id);
-        if (lid >= 0) hash_insert(table, a.hash_size, (uint32_t)lid);
-        __syncwarp();
-        // level 2 = distinct ids of the level-1 lists, minus seen / new / removed
-        int nf = 0;
-        for (int l = 0; l < a.k; ++l) {
-            const int32_t u = __shfl_sync(FULL, lid, l);
-            if (u < 0) continue;
-            const int32_t w = lane < a.k ? __ldg(a.nbr_ids + (size_t)u * a.k + lane) : -1;
-            bool keep = false;
-            if (w >= 0 && hash_insert(table, a.hash_size, (uint32_t)w))
-                keep = (uint32_t)w < a.n && !((__ldg(a.removed + (w >> 5)) >> (w & 31)) & 1u);
-            const unsigned km = __ballot_sync(FULL, keep);
-            if (keep) frontier[nf + __popc(km & ((1u << lane) - 1u))] = (uint32_t)w;
-            nf += __popc(km);
+        // seen = new, every node of the levels so far; an atomic test-and-set
+        // makes each id enter at most one level
+        uint32_t *seen;
+        if constexpr (SMEM_SEEN) {
+            seen = smem_seen + (size_t)wib * a.seen_words;
+            for (int64_t w = lane; w < a.seen_words; w += 32) seen[w] = 0u;
+        } else {
+            seen = a.seen + (size_t)i * a.seen_words;
         }
+        __syncwarp();
+        if (lane == 0) atomicOr(seen + (new_id >> 5), 1u << (new_id & 31));
+        if (lid >= 0) atomicOr(seen + ((uint32_t)lid >> 5), 1u << (lid & 31));
+        int32_t *level = a.frontier + (size_t)i * a.frontier_cap;  // the levels, one after another
+        if (lane < a.k) level[lane] = lid;
+        int lo = 0, hi = a.k;  // the current level is level[lo .. hi)
         __syncwarp();
         float qv[C::QF];
         load_query<ST_FP32, DP>(a.rows + (size_t)new_id * DP, qv);
-        for (int f0 = 0; f0 < nf; f0 += 32) {
-            const int nr = nf - f0 < 32 ? nf - f0 : 32;
-            const uint32_t w = lane < nr ? frontier[f0 + lane] : 0u;
-            const float d2 = gather_d2<ST_FP32, DP>(src, w, nr, qv);
-            bool has = false;
-            uint64_t key = 0;
-            if (lane < nr) {
-                key = pack_key(d2, new_id);
-                has = key < list_last_key(a, w);
+        const int per = 32 / a.k;  // parents expanded per step
+        const int pl = lane / a.k, el = lane % a.k;
+        for (int t = 2; t <= a.depth && lo < hi; ++t) {
+            // level t = distinct ids of the level t-1 lists, minus seen, minus
+            // removed nodes and points of this batch
+            int nhi = hi;
+            for (int p0 = lo; p0 < hi; p0 += per) {
+                int32_t u = -1;
+                if (pl < per && p0 + pl < hi) u = level[p0 + pl];
+                int32_t w = -1;
+                if (u >= 0) w = __ldg(a.nbr_ids + (size_t)u * a.k + el);
+                bool keep = false;
+                if (w >= 0) {
+                    const uint32_t bit = 1u << (w & 31);
+                    const uint32_t old = atomicOr(seen + ((uint32_t)w >> 5), bit);
+                    keep = !(old & bit) && (uint32_t)w < a.n &&
+                           !((__ldg(a.removed + (w >> 5)) >> (w & 31)) & 1u);
+                }
+                const unsigned km = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const int idx = nhi + __popc(km & lt_mask);
+                    if (idx < a.frontier_cap) level[idx] = w;
+                    else atomicOr(a.error_flags, (unsigned)ERR_OFFER_OVERFLOW);
+                }
+                nhi += __popc(km);
             }
-            push_offers(a, has, w, key);
+            if (nhi > a.frontier_cap) nhi = (int)a.frontier_cap;
+            __syncwarp();
+            // compute sim(new, node) for the level and offer `new` if needed
+            for (int f0 = hi; f0 < nhi; f0 += 32) {
+                const int nr = nhi - f0 < 32 ? nhi - f0 : 32;
+                const uint32_t w = lane < nr ? (uint32_t)level[f0 + lane] : 0u;
+                const float d2 = gather_d2<ST_FP32, DP>(src, w, nr, qv);
+                bool has = false;
+                uint64_t key = 0;
+                if (lane < nr) {
+                    key = pack_key(d2, new_id);
+                    has = key < list_last_key(a, w);
+                }
+                push_offers(a, has, w, key);
+            }
+            upd_evals += nhi - hi;
+            lo = hi;
+            hi = nhi;
         }
-        upd_evals = nf;
     }
     if (lane == 0) {
         a.counters[(size_t)i * NCTR + CTR_UPDATE_EVALS] = upd_evals;
@@ -295,13 +316,16 @@ static cudaError_t cross_dp(const CrossArgs &a, cudaStream_t s) {
 }
 template <int DP>
 static cudaError_t update_dp(const UpdateArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)UPD_WARPS * (a.hash_size + a.k * a.k) * sizeof(uint32_t);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(update_offers_kernel<DP>,
+    const int grid = (a.m + UPD_WARPS - 1) / UPD_WARPS;
+    const size_t smem = (size_t)UPD_WARPS * a.seen_words * sizeof(uint32_t);
+    if (a.depth >= 2 && update_seen_on_chip(a.seen_words)) {
+        cudaError_t e = cudaFuncSetAttribute(update_offers_kernel<DP, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        update_offers_kernel<DP, true><<<grid, UPD_WARPS * 32, smem, s>>>(a);
+    } else {
+        update_offers_kernel<DP, false><<<grid, UPD_WARPS * 32, 0, s>>>(a);
     }
-    update_offers_kernel<DP><<<(a.m + UPD_WARPS - 1) / UPD_WARPS, UPD_WARPS * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -343,6 +367,10 @@ cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_id
                                  int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     KNN_DP_DISPATCH(restore_dp, dp, rows, in_ids, n, k, nbr_ids, nbr_d2, bad, s)
+}
+
+bool update_seen_on_chip(int64_t seen_words) {
+    return (size_t)UPD_WARPS * seen_words * sizeof(uint32_t) <= UPD_SMEM_SEEN_MAX;
 }
 
 cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t s) {

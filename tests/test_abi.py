@@ -62,7 +62,7 @@ def _params(knn, **kw):
 
 @pytest.mark.parametrize("bad,status", [
     (dict(dim=0), -7), (dict(dim=257), -7), (dict(k=0), -7), (dict(k=33), -7),
-    (dict(depth=0), -7), (dict(depth=3), -7), (dict(storage=5), -1), (dict(speedup=0.0), -1),
+    (dict(depth=0), -7), (dict(depth=6), -7), (dict(storage=5), -1), (dict(speedup=0.0), -1),
     (dict(speedup=float("inf")), -1), (dict(expansion=float("nan")), -1),
     (dict(storage=1, rescore_mult=0), -7), (dict(storage=2, k=32, rescore_mult=5), -7),
     (dict(max_batch=0), -1), (dict(capacity=10), -3)])

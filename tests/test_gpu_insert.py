@@ -46,7 +46,7 @@ def edges(g, n, k):
     return ids.cpu().numpy(), sims.cpu().numpy()
 
 
-@pytest.mark.parametrize("speedup,depth", [(4.0, 2), (20.0, 2), (4.0, 1)])
+@pytest.mark.parametrize("speedup,depth", [(4.0, 2), (20.0, 2), (4.0, 1), (4.0, 3), (8.0, 5)])
 def test_single_point_inserts_match_sequential_oracle(knn, speedup, depth):
     """Both sides start from the oracle's exact graph.  After every insert the
     whole GPU graph must equal the oracle's, and the insert's counters and new
@@ -92,8 +92,8 @@ def _recall(ids, exact):
     return oracle.correct_edges(ids, exact) / exact.size
 
 
-@pytest.mark.parametrize("batch", [64, 256])
-def test_batched_inserts_recall_matches_sequential(knn, batch):
+@pytest.mark.parametrize("batch,depth", [(64, 2), (256, 2), (256, 3), (128, 4)])
+def test_batched_inserts_recall_matches_sequential(knn, batch, depth):
     mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=11)
     n0, na = 4000, 2048
     X0, Xs = mix.sample(n0, 1), mix.sample(na, 2)
@@ -101,10 +101,10 @@ def test_batched_inserts_recall_matches_sequential(knn, batch):
     X = np.vstack([X0, Xs])
     exact, _, _ = oracle.exact_knn(X, k)
     og = oracle.Graph.exact(X0, k, capacity=n0 + na)
-    og.insert_stream(Xs, speedup, e, 2, seed)
+    og.insert_stream(Xs, speedup, e, depth, seed)
     r_seq = _recall(og.ids, exact)
 
-    g = make_graph(knn, X0, k, speedup, e, seed, n0 + na, batch)
+    g = make_graph(knn, X0, k, speedup, e, seed, n0 + na, batch, depth)
     try:
         for b0 in range(0, na, batch):
             g.insert(cuda_tensor(Xs[b0:b0 + batch]))
@@ -122,7 +122,7 @@ def test_batched_inserts_recall_matches_sequential(knn, batch):
     for u in np.random.default_rng(0).choice(n0 + na, 40, replace=False):
         want = [oracle.similarity(X[u], X[v]) for v in got[u]]
         assert rel_err(sims[u], want).max() <= 1e-5
-    assert st["inserts"] == na and st["update_evals"] <= na * k * k
+    assert st["inserts"] == na and st["update_evals"] <= na * sum(k ** t for t in range(2, depth + 1))
 
 
 def test_insert_edge_cases(knn):
