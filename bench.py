@@ -51,6 +51,12 @@ def parse_args():
     ap.add_argument("--speedup", type=float, default=4.0)
     ap.add_argument("--expansion", type=float, default=5.0)
     ap.add_argument("--depth", type=int, default=2)
+    ap.add_argument("--workload", default="plain", choices=("small", "plain", "precision"),
+                    help="small: d=16, 1,000 + one at a time; plain: d=128, 100,000 + 1,024-point "
+                         "batches (default); precision: d=96, 1,000,000 + 1,024-point batches, k=20")
+    ap.add_argument("--storage", default=None, choices=("fp32", "bf16", "fp8"),
+                    help="searched copy of the rows (default: fp32; bf16 for precision)")
+    ap.add_argument("--rescore-mult", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -143,6 +149,21 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def aggregate_replicas(dist, local_ms: float, local_units: int, device=None):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    and the units all ranks processed (barrier on both sides of the timed
+    region is the caller's).  With dist None (one process) they are the
+    local ones."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return local_ms, local_units
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def edge_recall(torch, ids, exact):
     """Directed edges u->v present in both graphs, over n*k (Sec. 8.5's e_c)."""
     hit = 0
@@ -229,7 +250,7 @@ def run_reference(args, W):
     value = rate * n_avg / n_full_avg
     sample = (f"FP64 oracle, Algorithm 1 on 1 thread: each step inserts {per_step} stream "
               f"points one at a time into the oracle's own graph (exact graph of the first "
-              f"20000 initial points, then the inserts so far); "
+              f"{n_start - args.warmup * per_step} initial points, then the inserts so far); "
               f"{rate:.1f} inserts/s at mean n {n_avg:.0f}, scaled by n/speedup to the GPU "
               f"run's mean n {n_full_avg:.0f}")
     line = {
@@ -245,12 +266,25 @@ def run_reference(args, W):
     print(json.dumps(line), flush=True)
 
 
+def pick_workload(args):
+    from paper_1602_06819_gb300 import inputs
+    W = {"small": inputs.SMALL_D16, "plain": inputs.PLAIN_D128,
+         "precision": inputs.PRECISION_D96}[args.workload]
+    if args.storage is None:
+        args.storage = "bf16" if args.workload == "precision" else "fp32"
+    return W
+
+
 def workload_config(args, W):
-    return {"workload": W.name, "n_init": W.n_init, "d": W.mixture.d, "k": W.k,
-            "components": W.mixture.components, "batch": W.batch,
-            "speedup": args.speedup, "expansion": args.expansion, "depth": args.depth,
-            "similarity": "1/(1+L2)", "inserts_timed_per_gpu": args.steps * W.batch,
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+    cfg = {"workload": W.name, "n_init": W.n_init, "d": W.mixture.d, "k": W.k,
+           "components": W.mixture.components, "batch": W.batch,
+           "speedup": args.speedup, "expansion": args.expansion, "depth": args.depth,
+           "storage": args.storage, "similarity": "1/(1+L2)",
+           "inserts_timed_per_gpu": args.steps * W.batch,
+           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+    if args.storage != "fp32":
+        cfg["rescore"] = f"FP32 re-score of the best {args.rescore_mult}k screening candidates"
+    return cfg
 
 
 # ---------------------------------------------------------------------------
@@ -259,7 +293,7 @@ def workload_config(args, W):
 
 def main():
     args = parse_args()
-    from paper_1602_06819_gb300.inputs import PLAIN_D128 as W
+    W = pick_workload(args)
     if args.impl == "reference":
         run_reference(args, W)
         return
@@ -285,9 +319,12 @@ def main():
     Xs_host = W.mixture.sample(n_stream, W.seed_stream + 1000 * rank)
     Xs = torch.from_numpy(Xs_host).cuda()
     capacity = W.n_init + n_stream
-    cfg = knn.GraphConfig(dim=W.mixture.d, k=W.k, depth=args.depth, speedup=args.speedup,
-                          expansion=args.expansion, max_batch=B, seed=W.seed_search + rank,
-                          capacity=capacity)
+    storage = {"fp32": knn.KNN_STORAGE_FP32, "bf16": knn.KNN_STORAGE_BF16,
+               "fp8": knn.KNN_STORAGE_FP8_E4M3}[args.storage]
+    cfg = knn.GraphConfig(dim=W.mixture.d, k=W.k, depth=args.depth, storage=storage,
+                          speedup=args.speedup, expansion=args.expansion,
+                          rescore_mult=args.rescore_mult, max_batch=B,
+                          seed=W.seed_search + rank, capacity=capacity)
 
     # exact initial graph (timed on its own, not part of a step)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -328,12 +365,7 @@ def main():
     clk = clocks.stop()
     st1 = g.stats()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    inserts = K * B * world
+    total_ms, inserts = aggregate_replicas(dist, sum(step_ms), K * B, device="cuda")
     value = inserts / (total_ms / 1e3)
 
     # edge recall and Q of the final graph against its exact graph (Sec. 8.5)
@@ -349,14 +381,16 @@ def main():
     del exact, online, Xall
 
     # roofline of the dominant kernel (the iGNNS search)
-    row_bytes = 4 * 128
+    dp = next(v for v in (16, 32, 64, 96, 128, 256) if W.mixture.d <= v)
+    row_bytes = {"fp32": 4 * dp, "bf16": 2 * dp, "fp8": dp + 4}[args.storage]
     d_evals = st1["search_evals"] - st0["search_evals"]
     d_adj = st1["adjacency_reads"] - st0["adjacency_reads"]
-    alg_bytes_launch = (d_evals * row_bytes + d_adj * W.k * 4 + K * B * row_bytes) / K
+    alg_bytes_launch = (d_evals * row_bytes + d_adj * W.k * 4 + K * B * 4 * dp) / K
     search_ms = phases["search"] / K
     achieved = alg_bytes_launch / (search_ms / 1e3) / 1e9
     peak, peak_src = measured_peaks()
-    traffic, traffic_src = profiled_traffic()
+    traffic, traffic_src = (profiled_traffic() if (args.workload, args.storage) == ("plain", "fp32")
+                            else (None, None))
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     g.close()
     del g
@@ -377,11 +411,8 @@ def main():
         for i in range(K):
             g2.insert(Xp[(Wm + i) * B:(Wm + i + 1) * B], ids_h, nbrs_h)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([wall], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
+        wall_ms, _ = aggregate_replicas(dist, 1e3 * (time.perf_counter() - t0), K * B, device="cuda")
+        wall = wall_ms / 1e3
         g2.close()
         e2e = {"value": inserts / wall, "unit": UNIT,
                "h2d_bytes_per_step": B * W.mixture.d * 4,
@@ -397,18 +428,19 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": total_ms / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, W),
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[args.storage],
+            "data": "synthetic", "config": workload_config(args, W),
             "recall": {"edge_recall": recall, "target": RECALL_TARGET,
                        "target_met": recall >= RECALL_TARGET, "Q": q, "n_final": n_final},
             "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
-                           "unit": "one 1,024-point insert batch"},
+                           "unit": f"one {B:,}-point insert batch"},
             "evals_per_insert": {"search": d_evals / (K * B),
                                  "update": (st1["update_evals"] - st0["update_evals"]) / (K * B),
                                  "cross": (st1["cross_evals"] - st0["cross_evals"]) / (K * B)},
             "phases_ms_per_step": {p: v / K for p, v in phases.items()},
             "exact_build_ms": exact_ms,
-            "roofline": {"kernel": "ignns_search_kernel<fp32,128>", "bound": "hbm",
+            "roofline": {"kernel": f"ignns_search_kernel<{args.storage},{dp}>", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
                          "traffic": traffic, "traffic_source": traffic_src,
