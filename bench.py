@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "inserts+queries/sec at edge recall≥0.95 vs exact; p50/p99 latency; HBM GB/s"
 UNIT = "inserts/s"
 RECALL_TARGET = 0.95
+FALLBACK_BF16_TFLOPS = 1900.0
 FALLBACK_HBM_GBS = 6800.0
 SEARCH_PROFILE = os.path.join(ROOT, "profiles", "ignns_search_fp32_d128_n100k_batch1024.md")
 SEARCH_SOURCES = ("common.cuh", "search.cuh", "search_fp32.cu")
@@ -76,6 +77,34 @@ def measured_peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return FALLBACK_BF16_TFLOPS, "fallback"
+
+
+def exact_build_report(W, n, ms, info):
+    """The exact graph of n points (tensor-core screening + FP32 settling):
+    its time, how many rows the FP32 pass took, and the tensor-pipe view.
+    Algorithmic FLOPs are 2 n^2 d (one multiply-add per pair and dimension);
+    the screening executes 3 BF16 MMA passes over the dimension padded to
+    64 or 128 and the rows padded to 128."""
+    d = W.mixture.d
+    dpt = 64 if d <= 64 else 128
+    n_pad = -(-n // 128) * 128
+    alg = 2.0 * n * n * d
+    mma = 3 * 2.0 * n_pad * n_pad * dpt
+    peak, src = bf16_peak()
+    return {"n": n, "d": d, "k": W.k, "ms": ms, "path": info["path"],
+            "rows_redone": info["rows_redone"], "wait_errors": info["wait_errors"],
+            "algorithmic_tflops": alg / ms / 1e9, "mma_tflops": mma / ms / 1e9,
+            "tensor_peak": peak, "peak_source": f"{src} bf16_tflops",
+            "mma_frac": mma / ms / 1e9 / peak}
 
 
 def search_source_hash() -> str:
@@ -372,7 +401,13 @@ def main():
     n_final = st1["n"]
     Xall = torch.cat([X0, Xs[:n_final - W.n_init]])
     exact = torch.empty((n_final, W.k), dtype=torch.int64, device="cuda")
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    x0.record()
     knn.knn_exact_graph(Xall, W.k, exact)
+    x1.record()
+    torch.cuda.synchronize()
+    exact_gt = exact_build_report(W, n_final, x0.elapsed_time(x1), knn.knn_exact_last_info())
     online = torch.empty((n_final, W.k), dtype=torch.int64, device="cuda")
     g.edges(online)
     e_c = edge_recall(torch, online, exact)
@@ -440,6 +475,7 @@ def main():
                                  "cross": (st1["cross_evals"] - st0["cross_evals"]) / (K * B)},
             "phases_ms_per_step": {p: v / K for p, v in phases.items()},
             "exact_build_ms": exact_ms,
+            "exact_ground_truth": exact_gt,
             "roofline": {"kernel": f"ignns_search_kernel<{args.storage},{dp}>", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",

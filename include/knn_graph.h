@@ -217,6 +217,40 @@ KNN_API knn_status knn_exact_graph(const float *X, int64_t n, int32_t dim, int32
                                    int64_t *out_ids, float *out_sims, void *stream);
 
 /*
+ * How the brute-force exact graph (knn_exact_graph and the initial graph of
+ * knn_graph_create) is computed.  Both give the exact lists up to FP32
+ * rounding of the distances.
+ *   KNN_EXACT_AUTO          tensor cores when supported (dim <= 128,
+ *                           n >= 128), CUDA cores otherwise (default);
+ *   KNN_EXACT_CUDA_CORES    FP32 differences on CUDA cores for every pair;
+ *   KNN_EXACT_TENSOR_CORES  tensor cores, or KNN_ERR_UNSUPPORTED when the
+ *                           call does not qualify.
+ * The tensor-core path screens every pair with split-BF16 dot products
+ * (hi.hi + hi.lo + lo.hi, FP32 accumulation), keeps 32 candidates per node,
+ * re-scores them in FP32 and recomputes by brute force every node for which
+ * a proven bound on the screening error cannot exclude a better
+ * non-candidate; it reads back three counters and so synchronises the
+ * stream before returning.  The setting is process-wide.
+ */
+typedef enum knn_exact_path {
+    KNN_EXACT_AUTO = 0,
+    KNN_EXACT_CUDA_CORES = 1,
+    KNN_EXACT_TENSOR_CORES = 2
+} knn_exact_path;
+
+KNN_API knn_status knn_exact_set_path(int32_t path);
+
+/* What the calling thread's last exact build did. */
+typedef struct knn_exact_info {
+    int32_t path;          /* KNN_EXACT_CUDA_CORES or KNN_EXACT_TENSOR_CORES          */
+    uint32_t wait_errors;  /* tensor-core pipeline waits that gave up (rows redone)  */
+    int64_t n;             /* nodes                                                   */
+    int64_t rows_redone;   /* nodes settled by the FP32 brute-force pass             */
+} knn_exact_info;
+
+KNN_API knn_status knn_exact_last_info(knn_exact_info *out);
+
+/*
  * The query search of knn_graph_query_batch (FP32 rows, no removed nodes)
  * over a graph held in the caller's own device buffers, without any device
  * allocation.  The paper has no counterpart: this exists for callers that

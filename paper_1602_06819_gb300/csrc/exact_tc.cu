@@ -1,0 +1,543 @@
+// exact_tc.cu -- brute-force exact k-nn graph (Sec. 2.1) screened on the
+// tensor cores and settled in FP32.
+//
+// Ranking key of column v for row u: ||y_v||^2 - 2 x_u . y_v (the row
+// constant ||x_u||^2 is dropped).  The dot products run on tcgen05 with BF16
+// operands and FP32 accumulation, made nearly FP32-accurate by splitting each
+// value in two BF16 parts, x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), and
+// accumulating hi.hi + hi.lo + lo.hi.
+//
+// One CTA owns 128 rows and streams every column (12 warps):
+//   warp 0      TMA: the CTA's rows (hi and lo) once, then the column tiles,
+//               one 64-element K slice (hi and lo) per ring stage;
+//   warp 1      owns the TMEM allocation; one thread issues the MMAs of a
+//               128-column tile into one of two FP32 accumulators;
+//   warp 2      copies each tile's column norms beside its accumulator;
+//   warps 4..11 epilogue, two warpgroups: thread r of warpgroup h reads
+//               accumulator lane r (its row), columns 64h .. 64h+63 of each
+//               tile, forms their keys and keeps the 32 smallest it sees.
+// A key below the thread's current 32nd is only appended to a per-thread
+// buffer in shared memory; when some lane's buffer is half full the warp
+// merges all buffers into the sorted lists in lockstep, so the costly
+// insertions of the 32 rows of a warp run together instead of one lane at
+// a time.
+//
+// The screening is then made exact.  The 64 candidates of a row (32 per
+// warpgroup) are re-scored as FP32 squared differences and the k best kept.
+// Every other column has a screened key at least the smaller of the two
+// lists' 32nd keys; the row is accepted only if a proven bound on the
+// screening error shows that no such column can beat its k-th neighbour,
+// otherwise it is recomputed against every column in FP32 by the CUDA-core
+// kernel.  The lists therefore equal the exact ones up to FP32 rounding of
+// the distances.
+//
+// Every mbarrier wait is bounded.  A wait that gives up sets a bit of the
+// error word, and the rows of that CTA are marked for the FP32 pass, so the
+// result stays exact.
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_sm100.cuh"
+
+namespace knn {
+
+using namespace tc;
+
+constexpr int TC_ROWS = 128;            // rows per CTA (MMA M)
+constexpr int TC_COLS = 128;            // columns per tile (MMA N)
+constexpr int TC_CAND = 32;             // candidates kept per row and warpgroup
+constexpr int TC_NCAND = 2 * TC_CAND;   // candidates per row
+constexpr int TC_EPI = 256;             // epilogue threads
+constexpr int TC_BUF = 32;              // buffered keys per epilogue thread
+constexpr uint32_t TC_BOX = 128 * 128;  // bytes of one 128-row x 64-element BF16 box
+constexpr uint32_t TC_UNIT = 2 * TC_BOX;  // hi and lo boxes of one K slice
+constexpr uint64_t TC_WAIT = 2000000000ull;  // ns before a wait gives up
+
+// NBOX 64-element K slices per row (padded width 64 * NBOX)
+template <int NBOX>
+struct TcCfg {
+    static constexpr int STAGES = NBOX == 1 ? 4 : 3;  // ring of K slices
+    static constexpr uint32_t A_BYTES = NBOX * TC_UNIT;
+    static constexpr uint32_t BUF_BYTES = TC_BUF * TC_EPI * 8;
+    static constexpr int NBAR = 1 + 2 * STAGES + 6 + 1;  // a_full, b_full/empty, acc full/empty, yn_full, drain
+    static constexpr uint32_t SMEM =
+        1024 + A_BYTES + STAGES * TC_UNIT + BUF_BYTES + 2 * TC_COLS * 4 + NBAR * 8 + 16;
+    static_assert(SMEM <= 232448, "shared memory of one CTA");
+};
+
+// x -> (hi, lo) BF16 rows of width dpt (zero padded) and FP32 squared norms;
+// the largest norm goes to *norm_max (bit pattern of a non-negative float,
+// so that unsigned order is float order).  Rows n .. n_pad-1 get the norm
+// +inf, so that a column tile copied past the last row yields keys that are
+// never kept.
+__global__ void tc_split_kernel(const float *X, int64_t n, int64_t n_pad, int dp, int dpt, __nv_bfloat16 *hi,
+                                __nv_bfloat16 *lo, float *norm2, unsigned *norm_max) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= n) {
+        if (r < n_pad && lane == 0) norm2[r] = __int_as_float(0x7f800000);
+        return;
+    }
+    float s = 0.f;
+    for (int c = lane; c < dpt; c += 32) {
+        const float x = c < dp ? X[r * dp + c] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi[r * dpt + c] = h;
+        lo[r * dpt + c] = __float2bfloat16_rn(x - __bfloat162float(h));
+        s = fmaf(x, x, s);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
+    if (lane == 0) {
+        norm2[r] = s;
+        atomicMax(norm_max, __float_as_uint(sqrtf(s)));
+    }
+}
+
+// insert (k, v) into the ascending list of the TC_CAND smallest keys
+__device__ __forceinline__ void cand_insert(float (&key)[TC_CAND], int (&id)[TC_CAND], float k, int v) {
+#pragma unroll
+    for (int i = TC_CAND - 1; i > 0; --i) {
+        const bool shift = k < key[i - 1];
+        const bool here = !shift && k < key[i];
+        key[i] = shift ? key[i - 1] : (here ? k : key[i]);
+        id[i] = shift ? id[i - 1] : (here ? v : id[i]);
+    }
+    if (k < key[0]) {
+        key[0] = k;
+        id[0] = v;
+    }
+}
+
+template <int NBOX>
+__global__ void __launch_bounds__(384, 1)
+exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant__ CUtensorMap t_lo,
+                const float *__restrict__ norm2, int64_t n, int32_t *cand_id, float *cand_key,
+                unsigned *err) {
+    using Cfg = TcCfg<NBOX>;
+    constexpr int S = Cfg::STAGES;
+    extern __shared__ uint8_t tc_raw[];
+    // 128-byte swizzled tiles want 1024-byte aligned shared memory
+    uint8_t *sm = (uint8_t *)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *As = sm;                                   // NBOX x [hi box][lo box]
+    uint8_t *Bs = As + Cfg::A_BYTES;                    // S stages of [hi box][lo box]
+    uint64_t *sbuf = (uint64_t *)(Bs + S * TC_UNIT);    // [TC_BUF][TC_EPI] buffered (column, key bits)
+    float *s_yn = (float *)(sbuf + TC_BUF * TC_EPI);    // [2][TC_COLS] column norms
+    uint64_t *bars = (uint64_t *)(s_yn + 2 * TC_COLS);
+    uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + S;
+    uint64_t *acc_full = bars + 1 + 2 * S, *acc_empty = bars + 3 + 2 * S, *yn_full = bars + 5 + 2 * S;
+    uint64_t *drain = bars + 7 + 2 * S;
+    uint32_t *tmem_slot = (uint32_t *)(bars + Cfg::NBAR);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(b_full + s, 1);
+            mbar_init(b_empty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full + b, 1);
+            mbar_init(acc_empty + b, TC_EPI / 32);
+            mbar_init(yn_full + b, 1);
+        }
+        mbar_init(drain, 1);
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 2 * TC_COLS);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t row0 = (int64_t)blockIdx.x * TC_ROWS;
+    const int ntiles = (int)((n + TC_COLS - 1) / TC_COLS);
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        prefetch_tensormap(&t_hi);
+        prefetch_tensormap(&t_lo);
+        mbar_arrive_expect_tx(a_full, Cfg::A_BYTES);
+        for (int kb = 0; kb < NBOX; ++kb) {
+            tma_load_2d(As + kb * TC_UNIT, &t_hi, a_full, kb * 64, (int)row0);
+            tma_load_2d(As + kb * TC_UNIT + TC_BOX, &t_lo, a_full, kb * 64, (int)row0);
+        }
+        const int units = ntiles * NBOX;
+        int issued = 0;
+        for (int u = 0; u < units; ++u) {
+            const int s = u % S;
+            if (u >= S && !mbar_wait(b_empty + s, ((u / S) - 1) & 1, TC_WAIT)) {
+                atomicOr(err, 1u);
+                break;
+            }
+            const int t = u / NBOX, kb = u % NBOX;
+            uint8_t *B = Bs + s * TC_UNIT;
+            mbar_arrive_expect_tx(b_full + s, TC_UNIT);
+            tma_load_2d(B, &t_hi, b_full + s, kb * 64, t * TC_COLS);
+            tma_load_2d(B + TC_BOX, &t_lo, b_full + s, kb * 64, t * TC_COLS);
+            issued = u + 1;
+        }
+        // no copy may still be in flight when the CTA exits
+        bool landed = mbar_wait(a_full, 0, TC_WAIT);
+        for (int u = issued > S ? issued - S : 0; u < issued; ++u)
+            landed = mbar_wait(b_full + u % S, (u / S) & 1, TC_WAIT) && landed;
+        if (!landed) atomicOr(err, 32u);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer: acc = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+        constexpr uint32_t idesc = idesc_bf16_f32(TC_ROWS, TC_COLS);
+        bool ok = mbar_wait(a_full, 0, TC_WAIT);
+        if (!ok) atomicOr(err, 2u);
+        for (int t = 0; ok && t < ntiles; ++t) {
+            const int buf = t & 1;
+            if (t >= 2 && !mbar_wait(acc_empty + buf, ((t / 2) - 1) & 1, TC_WAIT)) {
+                atomicOr(err, 8u);
+                break;
+            }
+            const uint32_t d = tmem + buf * TC_COLS;
+            for (int kb = 0; kb < NBOX; ++kb) {
+                const int u = t * NBOX + kb, s = u % S;
+                if (!mbar_wait(b_full + s, (u / S) & 1, TC_WAIT)) {
+                    atomicOr(err, 4u);
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint64_t ah = sdesc_k_sw128(smem_u32(As + kb * TC_UNIT));
+                const uint64_t al = sdesc_k_sw128(smem_u32(As + kb * TC_UNIT + TC_BOX));
+                const uint64_t bh = sdesc_k_sw128(smem_u32(Bs + s * TC_UNIT));
+                const uint64_t bl = sdesc_k_sw128(smem_u32(Bs + s * TC_UNIT + TC_BOX));
+                for (int kk = 0; kk < 4; ++kk) {  // K step of 16 BF16 = 32 bytes = 2 descriptor units
+                    mma_bf16(d, ah + 2 * kk, bh + 2 * kk, idesc, (kb | kk) != 0);
+                    mma_bf16(d, ah + 2 * kk, bl + 2 * kk, idesc, 1u);
+                    mma_bf16(d, al + 2 * kk, bh + 2 * kk, idesc, 1u);
+                }
+                mma_commit(b_empty + s);
+            }
+            if (ok) mma_commit(acc_full + buf);
+        }
+        // every MMA issued has finished before TMEM is released
+        mma_commit(drain);
+        if (!mbar_wait(drain, 0, TC_WAIT)) atomicOr(err, 64u);
+    } else if (warp == 2 && lane == 0) {
+        // ---- column norms of tile t into s_yn[t % 2], once the epilogue has
+        // released that buffer (with the accumulator of tile t - 2)
+        int issued = 0;
+        for (int t = 0; t < ntiles; ++t) {
+            const int buf = t & 1;
+            if (t >= 2 && !mbar_wait(acc_empty + buf, ((t / 2) - 1) & 1, TC_WAIT)) {
+                atomicOr(err, 128u);
+                break;
+            }
+            mbar_arrive_expect_tx(yn_full + buf, TC_COLS * 4);
+            bulk_load(s_yn + buf * TC_COLS, norm2 + (int64_t)t * TC_COLS, TC_COLS * 4, yn_full + buf);
+            issued = t + 1;
+        }
+        bool landed = true;
+        for (int t = issued > 2 ? issued - 2 : 0; t < issued; ++t)
+            landed = mbar_wait(yn_full + (t & 1), (t / 2) & 1, TC_WAIT) && landed;
+        if (!landed) atomicOr(err, 256u);
+    } else if (warp >= 4) {
+        // ---- epilogue: thread r of warpgroup h owns row row0 + r (TMEM lane r)
+        const int te = threadIdx.x - 128;
+        const int h = te >> 7, r = te & 127;
+        const int64_t row = row0 + r;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        uint64_t *mybuf = sbuf + te;  // entry e at mybuf[e * TC_EPI]
+        float key[TC_CAND];
+        int id[TC_CAND];
+#pragma unroll
+        for (int i = 0; i < TC_CAND; ++i) {
+            key[i] = __int_as_float(0x7f800000);
+            id[i] = -1;
+        }
+        float thr = __int_as_float(0x7f800000);  // current 32nd key
+        int cnt = 0;                              // buffered entries
+        auto flush = [&]() {
+            const int m = __reduce_max_sync(FULL, cnt);
+#pragma unroll 1
+            for (int e = 0; e < m; ++e) {
+                if (e < cnt) {
+                    const uint2 ent = reinterpret_cast<const uint2 *>(mybuf)[e * TC_EPI];
+                    const float kk = __uint_as_float(ent.y);
+                    const int col = (int)ent.x;
+                    if (kk < key[TC_CAND - 1] && (int64_t)col != row) cand_insert(key, id, kk, col);
+                }
+            }
+            cnt = 0;
+            thr = key[TC_CAND - 1];
+        };
+        bool ok = true;
+        for (int t = 0; t < ntiles; ++t) {
+            const int buf = t & 1;
+            const int64_t c_base = (int64_t)t * TC_COLS;
+            if (ok)
+                ok = __all_sync(FULL, mbar_wait(acc_full + buf, (t / 2) & 1, TC_WAIT) &&
+                                          mbar_wait(yn_full + buf, (t / 2) & 1, TC_WAIT));
+            if (!ok && lane == 0) atomicOr(err, 16u);
+            fence_after_sync();
+            if (ok) {
+                const uint32_t ta = tmem + lane_base + buf * TC_COLS + 64 * h;
+                const float *yn = s_yn + buf * TC_COLS + 64 * h;
+                const uint32_t col0 = (uint32_t)c_base + 64 * h;
+                // 16 columns: keys, then per group of 4 their minimum; only
+                // the groups where some lane of the warp has a key below its
+                // threshold run the appends, so that the common case takes no
+                // divergent branch
+                auto scan16 = [&](const uint32_t(&v)[16], int c) {
+                    float kv[16];
+#pragma unroll
+                    for (int j4 = 0; j4 < 4; ++j4) {
+                        const float4 y = *reinterpret_cast<const float4 *>(yn + c + 4 * j4);
+                        kv[4 * j4 + 0] = fmaf(-2.0f, __uint_as_float(v[4 * j4 + 0]), y.x);
+                        kv[4 * j4 + 1] = fmaf(-2.0f, __uint_as_float(v[4 * j4 + 1]), y.y);
+                        kv[4 * j4 + 2] = fmaf(-2.0f, __uint_as_float(v[4 * j4 + 2]), y.z);
+                        kv[4 * j4 + 3] = fmaf(-2.0f, __uint_as_float(v[4 * j4 + 3]), y.w);
+                    }
+                    unsigned g = 0;
+#pragma unroll
+                    for (int j4 = 0; j4 < 4; ++j4) {
+                        const float mn =
+                            fminf(fminf(kv[4 * j4], kv[4 * j4 + 1]), fminf(kv[4 * j4 + 2], kv[4 * j4 + 3]));
+                        g |= (unsigned)(mn < thr) << j4;
+                    }
+                    g = __reduce_or_sync(FULL, g);
+                    if (g) {
+#pragma unroll
+                        for (int j4 = 0; j4 < 4; ++j4) {
+                            if ((g >> j4) & 1u) {
+#pragma unroll
+                                for (int jj = 0; jj < 4; ++jj) {
+                                    const int j = 4 * j4 + jj;
+                                    const bool p = kv[j] < thr;
+                                    if (p)
+                                        reinterpret_cast<uint2 *>(mybuf)[cnt * TC_EPI] =
+                                            make_uint2(col0 + c + j, __float_as_uint(kv[j]));
+                                    cnt += p;
+                                }
+                            }
+                        }
+                        if (__any_sync(FULL, cnt > TC_BUF - 16)) flush();
+                    }
+                };
+#pragma unroll 1
+                for (int c = 0; c < 64; c += 32) {
+                    uint32_t v[32];
+                    tmem_ld32_async(ta + c, v);
+                    tmem_wait_ld(v);
+                    scan16(reinterpret_cast<const uint32_t(&)[16]>(v[0]), c);
+                    scan16(reinterpret_cast<const uint32_t(&)[16]>(v[16]), c + 16);
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + buf);
+        }
+        flush();
+        if (row < n) {
+            int32_t *ci = cand_id + row * TC_NCAND + h * TC_CAND;
+            float *ck = cand_key + row * TC_NCAND + h * TC_CAND;
+#pragma unroll
+            for (int i = 0; i < TC_CAND; ++i) {
+                ci[i] = ok ? id[i] : -1;  // no candidates: the FP32 pass takes the row
+                ck[i] = key[i];
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, 2 * TC_COLS);
+    }
+}
+
+// Bound on |screened key - true key| for a row of norm xnorm (and FP32
+// squared norm xn) against any column, whose norm is at most ymax:
+// * split: x = hi + lo + e with |e| <= 2^-18 |x|, and the dropped lo.lo term,
+//   leave at most 3 * 2^-18 |x_i| |y_i| per product; 4 * 2^-18 covers the
+//   second-order terms;
+// * accumulation: the BF16 products are exact in FP32; each of the 3 dpt
+//   additions is taken to lose up to 2^-23 (truncation) of the running sum,
+//   itself at most sum |x_i y_i| <= xnorm * ymax;
+// * the key is -2 times the dot product plus a column norm with an FP32
+//   error of (dpt + 2) 2^-24 ymax^2; the fma rounds once more.
+// A factor of 2 on the whole covers the FP32 evaluation of the test itself.
+__device__ __forceinline__ float screening_error(float xnorm, float xn, float ymax, int dpt) {
+    const float dot = (4.0f * 0x1p-18f + 3.0f * dpt * 0x1p-23f) * xnorm * ymax;
+    const float rest = (dpt + 4) * 0x1p-24f * (xn + 3.0f * ymax * ymax);
+    return 2.0f * (2.0f * dot + rest);
+}
+
+// One warp per row: FP32 re-score of the 64 candidates, the k best written
+// as the row's list, and the exactness test of the screening.  Rows that
+// fail are appended to `redo`.
+template <int DP>
+__global__ void tc_rescore_kernel(const float *X, const float *norm2, const unsigned *norm_max, int64_t n, int k,
+                                  int dpt, const int32_t *cand_id, const float *cand_key, int32_t *out_ids,
+                                  float *out_d2, int32_t *redo, unsigned *redo_count) {
+    using C = RowCfg<ST_FP32, DP>;
+    const int lane = threadIdx.x & 31;
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (u >= n) return;  // warp-uniform
+    float qv[C::QF];
+    load_query<ST_FP32, DP>(X + u * DP, qv);
+    const RowSource src{reinterpret_cast<const uint8_t *>(X), nullptr};
+    WarpTop<1> top;
+    top.init(k);
+    int full = 0;  // warpgroup lists holding TC_CAND candidates
+    float thr = __int_as_float(0x7f800000);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int32_t cid = cand_id[u * TC_NCAND + h * TC_CAND + lane];
+        const int nc = __popc(__ballot_sync(FULL, cid >= 0));  // candidates fill a prefix
+        const float d2 = gather_d2<ST_FP32, DP>(src, cid >= 0 ? (uint32_t)cid : 0u, nc, qv);
+        for (int i = 0; i < nc; ++i)
+            top.offer(pack_key(__shfl_sync(FULL, d2, i), (uint32_t)__shfl_sync(FULL, cid, i)));
+        full += nc == TC_CAND;
+        thr = fminf(thr, cand_key[u * TC_NCAND + h * TC_CAND + TC_CAND - 1]);
+    }
+    if (lane < k) {
+        const uint64_t key = top.e[0];
+        out_ids[u * k + lane] = key == KEY_EMPTY ? -1 : (int32_t)key_id(key);
+        out_d2[u * k + lane] = key == KEY_EMPTY ? __int_as_float(0x7f800000) : key_d2(key);
+    }
+    // Every column outside the candidates has a screened key >= thr, so a
+    // true squared distance >= thr + ||x||^2 - E.  The k-th re-scored
+    // distance (FP32, relative error below (DP + 2) 2^-24) must lie below.
+    bool exact = false;
+    if (full == 2) {
+        const float dk = key_d2(top.entry(k - 1));
+        const float xn = norm2[u];
+        const float E = screening_error(sqrtf(xn), xn, __uint_as_float(*norm_max), dpt);
+        exact = dk * (1.0f + (DP + 2) * 0x1p-23f) < thr + xn - E;
+    }
+    if (!exact && lane == 0) redo[atomicAdd(redo_count, 1u)] = (int32_t)u;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// rows x dpt BF16 matrix, boxes of 128 rows x 64 elements, 128-byte swizzle;
+// rows past the end read as zeros
+static bool bf16_rows_map(CUtensorMap *m, const void *ptr, int64_t rows, int dpt) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)dpt, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)dpt * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)TC_ROWS};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int tc_width(int dp) { return dp <= 64 ? 64 : 128; }
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+bool exact_tc_supported(int dp, int64_t n, int k, const uint32_t *removed) {
+    return removed == nullptr && dp <= 128 && n >= TC_ROWS && n < (int64_t)INT32_MAX && k >= 1 &&
+           k <= TC_CAND && tensor_map_encoder() != nullptr;
+}
+
+// scratch, each part 256-byte aligned: hi, lo, norm2, cand_id, cand_key,
+// redo, counters[16] = {norm max, redo count, wait error, ...}, partial
+// lists of the FP32 pass
+size_t exact_tc_scratch_bytes(int64_t n, int dp) {
+    const size_t dpt = tc_width(dp);
+    const size_t n_pad = (size_t)(n + TC_COLS - 1) / TC_COLS * TC_COLS;
+    return 2 * align256((size_t)n * dpt * 2) + align256(n_pad * 4) + 2 * align256((size_t)n * TC_NCAND * 4) +
+           align256((size_t)n * 4) + 256 + align256((size_t)EXACT_PARTIAL_SLOTS * 32 * 8);
+}
+
+template <int NBOX>
+static cudaError_t tc_screen(const CUtensorMap &th, const CUtensorMap &tl, const float *norm2, int64_t n,
+                             int32_t *cid, float *ckey, unsigned *err, cudaStream_t s) {
+    const size_t smem = TcCfg<NBOX>::SMEM;
+    cudaError_t e =
+        cudaFuncSetAttribute(exact_tc_kernel<NBOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    exact_tc_kernel<NBOX><<<(unsigned)((n + TC_ROWS - 1) / TC_ROWS), 384, smem, s>>>(th, tl, norm2, n, cid, ckey,
+                                                                                     err);
+    return cudaGetLastError();
+}
+
+template <int DP>
+static cudaError_t tc_rescore(const ExactArgs &a, int dpt, const float *norm2, unsigned *counters,
+                              const int32_t *cid, const float *ckey, int32_t *redo, cudaStream_t s) {
+    const int64_t threads = a.n * 32;
+    tc_rescore_kernel<DP><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        a.X, norm2, counters, a.n, a.k, dpt, cid, ckey, a.out_ids, a.out_d2, redo, counters + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned **counters_out, cudaStream_t s) {
+    const int dpt = tc_width(dp);
+    uint8_t *p = static_cast<uint8_t *>(scratch);
+    auto take = [&](size_t bytes) {
+        uint8_t *q = p;
+        p += align256(bytes);
+        return q;
+    };
+    auto *hi = (__nv_bfloat16 *)take((size_t)a.n * dpt * 2);
+    auto *lo = (__nv_bfloat16 *)take((size_t)a.n * dpt * 2);
+    const int64_t n_pad = (a.n + TC_COLS - 1) / TC_COLS * TC_COLS;
+    auto *norm2 = (float *)take((size_t)n_pad * 4);
+    auto *cid = (int32_t *)take((size_t)a.n * TC_NCAND * 4);
+    auto *ckey = (float *)take((size_t)a.n * TC_NCAND * 4);
+    auto *redo = (int32_t *)take((size_t)a.n * 4);
+    auto *counters = (unsigned *)take(64);
+    auto *partial = (uint64_t *)take((size_t)EXACT_PARTIAL_SLOTS * 32 * 8);
+    *counters_out = counters;
+    CUtensorMap th, tl;
+    if (!bf16_rows_map(&th, hi, a.n, dpt) || !bf16_rows_map(&tl, lo, a.n, dpt)) return cudaErrorNotSupported;
+    cudaError_t e = cudaMemsetAsync(counters, 0, 64, s);
+    if (e != cudaSuccess) return e;
+    tc_split_kernel<<<(unsigned)((n_pad * 32 + 255) / 256), 256, 0, s>>>(a.X, a.n, n_pad, dp, dpt, hi, lo,
+                                                                          norm2, counters);
+    e = dpt == 64 ? tc_screen<1>(th, tl, norm2, a.n, cid, ckey, counters + 2, s)
+                  : tc_screen<2>(th, tl, norm2, a.n, cid, ckey, counters + 2, s);
+    if (e != cudaSuccess) return e;
+    switch (dp) {
+        case 16: e = tc_rescore<16>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
+        case 32: e = tc_rescore<32>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
+        case 64: e = tc_rescore<64>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
+        case 96: e = tc_rescore<96>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
+        case 128: e = tc_rescore<128>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    // the rows the screening could not settle, against every column in FP32;
+    // their number decides how the columns are split
+    unsigned nredo = 0;
+    e = cudaMemcpyAsync(&nredo, counters + 1, sizeof nredo, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || nredo == 0) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    ExactArgs rest = a;
+    rest.rows = redo;
+    rest.row_count = counters + 1;
+    rest.col_segments = exact_col_segments(nredo, a.n, sms);
+    rest.partial = partial;
+    return launch_exact(dp, rest, s);
+}
+
+}  // namespace knn

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -130,6 +131,48 @@ static bool is_device_ptr(const void *p) {
         return false;
     }
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// exact graph: CUDA cores or tensor cores (knn_exact_set_path)
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_exact_path{KNN_EXACT_AUTO};
+static thread_local knn_exact_info g_exact_info{};
+
+// The exact lists of ea.X into ea.out_ids / ea.out_d2.  The tensor-core path
+// allocates its scratch on the stream and reads its counters back, so it
+// returns with the stream drained.  *launches grows by the kernels launched.
+static knn_status run_exact(int dp, const ExactArgs &ea, cudaStream_t s, int64_t *launches) {
+    const int mode = g_exact_path.load();
+    const bool tc = exact_tc_supported(dp, ea.n, ea.k, ea.removed);
+    if (mode == KNN_EXACT_TENSOR_CORES && !tc)
+        return fail(KNN_ERR_UNSUPPORTED, "tensor-core exact build needs padded dim <= 128, n >= 128 (dp %d, n %lld)",
+                    dp, (long long)ea.n);
+    knn_exact_info info{};
+    info.n = ea.n;
+    if (mode == KNN_EXACT_CUDA_CORES || !tc) {
+        CU(launch_exact(dp, ea, s));
+        info.path = KNN_EXACT_CUDA_CORES;
+        *launches += 1;
+        g_exact_info = info;
+        return KNN_OK;
+    }
+    void *scratch = nullptr;
+    CU(cudaMallocAsync(&scratch, exact_tc_scratch_bytes(ea.n, dp), s));
+    unsigned *counters = nullptr;
+    unsigned host[3] = {0, 0, 0};
+    cudaError_t e = launch_exact_tc(dp, ea, scratch, &counters, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, counters, sizeof host, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) return fail(KNN_ERR_CUDA, "tensor-core exact build: %s", cudaGetErrorString(e));
+    *launches += 4;
+    info.path = KNN_EXACT_TENSOR_CORES;
+    info.rows_redone = host[1];
+    info.wait_errors = host[2];
+    g_exact_info = info;
+    return KNN_OK;
 }
 
 static int64_t budget_of(int64_t n, double speedup) {
@@ -418,7 +461,7 @@ KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_
         ea.out_d2 = g->nbr_d2;
         ea.n = n_init;
         ea.k = g->p.k;
-        CU(launch_exact(g->dp, ea, s));
+        TRY(run_exact(g->dp, ea, s, &g->launches));
         CU(cudaStreamSynchronize(s));
         return KNN_OK;
     };
@@ -763,7 +806,8 @@ KNN_API knn_status knn_exact_graph(const float *X, int64_t n, int32_t dim, int32
     ea.out_d2 = d2;
     ea.n = n;
     ea.k = k;
-    CU(launch_exact(dp, ea, s));
+    int64_t launches = 0;
+    TRY(run_exact(dp, ea, s, &launches));
     if (!ids_dev) CU(cudaMallocAsync(&ids_tmp, (size_t)n * k * 8, s));
     if (out_sims && !sims_dev) CU(cudaMallocAsync(&sims_tmp, (size_t)n * k * 4, s));
     CU(launch_lists_to_output(ids, d2, n, k, ids_dev ? out_ids : ids_tmp,
@@ -773,6 +817,19 @@ KNN_API knn_status knn_exact_graph(const float *X, int64_t n, int32_t dim, int32
     for (void *p : {(void *)rows, (void *)ids, (void *)d2, (void *)xin, (void *)ids_tmp, (void *)sims_tmp})
         if (p) CU(cudaFreeAsync(p, s));
     if (ids_tmp || sims_tmp) CU(cudaStreamSynchronize(s));
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_exact_set_path(int32_t path) {
+    if (path != KNN_EXACT_AUTO && path != KNN_EXACT_CUDA_CORES && path != KNN_EXACT_TENSOR_CORES)
+        return fail(KNN_ERR_INVALID_ARG, "unknown exact path %d", path);
+    g_exact_path.store(path);
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_exact_last_info(knn_exact_info *out) {
+    if (!out) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    *out = g_exact_info;
     return KNN_OK;
 }
 

@@ -126,7 +126,19 @@ struct ExactArgs {
     float *out_d2;
     int64_t n;
     int32_t k;
+    // nullable: compute only the rows rows[0 .. *row_count) (device memory)
+    const int32_t *rows = nullptr;
+    const unsigned *row_count = nullptr;
+    // > 1: the columns are split in this many segments, one block column
+    // each; their lists go to `partial` ([row slot][segment][32] packed keys,
+    // exact_partial_slots() row slots at most) and are merged afterwards
+    int32_t col_segments = 1;
+    uint64_t *partial = nullptr;
 };
+// column segments that let a pass over `rows` listed rows fill the GPU, and
+// the row slots x segments of partial lists that choice can need
+int exact_col_segments(int64_t rows, int64_t n, int sm_count);
+constexpr int64_t EXACT_PARTIAL_SLOTS = 64 * 2 * 2 * 160;
 
 // supported padded dimensions
 bool supported_dp(int dp);
@@ -143,6 +155,14 @@ cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t s);
 // true when Update keeps its seen bitsets (seen_words words each) on chip
 bool update_seen_on_chip(int64_t seen_words);
 cudaError_t launch_exact(int dp, const ExactArgs &a, cudaStream_t s);
+// tensor-core screening + FP32 settling (exact_tc.cu): usable when
+// exact_tc_supported(); `scratch` holds exact_tc_scratch_bytes(n, dp) device
+// bytes; *counters_out receives the device address of three words
+// {largest norm, rows settled by brute force, wait-error bits}.  Reads the
+// number of unsettled rows back, so it synchronises the stream once.
+bool exact_tc_supported(int dp, int64_t n, int k, const uint32_t *removed);
+size_t exact_tc_scratch_bytes(int64_t n, int dp);
+cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned **counters_out, cudaStream_t s);
 // snapshot restore: copy int64 lists (checking every id) and recompute their d2
 cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,
                                  int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s);

@@ -43,8 +43,10 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
 EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
             "knn_graph_remove", "knn_graph_get_edges", "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_stats",
-            "knn_graph_destroy", "knn_exact_graph", "knn_search_noalloc", "knn_last_error",
-            "knn_version")
+            "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
+            "knn_search_noalloc", "knn_last_error", "knn_version")
+
+EXACT_PATHS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
 
 PHASES = ("store", "search", "rescore", "cross", "offers", "merge")
 
@@ -65,6 +67,11 @@ class KnnStats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class KnnExactInfo(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("wait_errors", ctypes.c_uint32), ("n", ctypes.c_int64),
+                ("rows_redone", ctypes.c_int64)]
 
 
 class KnnError(RuntimeError):
@@ -92,6 +99,8 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_stats": (I32, [P, ctypes.POINTER(KnnStats)]),
         "knn_graph_destroy": (None, [P]),
         "knn_exact_graph": (I32, [P, I64, I32, I32, P, P, P]),
+        "knn_exact_set_path": (I32, [I32]),
+        "knn_exact_last_info": (I32, [ctypes.POINTER(KnnExactInfo)]),
         "knn_search_noalloc": (I32, [P, I64, I32, P, I32, P, I64, I32, ctypes.c_double,
                                      ctypes.c_double, U64, U64, P, P, P]),
         "knn_last_error": (ctypes.c_char_p, []),
@@ -224,6 +233,20 @@ def knn_exact_graph(X, k: int, out_ids, out_sims=None, stream=None) -> None:
     _check_dtype(out_sims, "float32", "out_sims")
     _check(lib.knn_exact_graph(_ptr(X), X.shape[0], X.shape[1], k, _ptr(out_ids), _ptr(out_sims),
                                _stream(stream)), "knn_exact_graph")
+
+
+def knn_exact_set_path(path: str) -> None:
+    """Process-wide choice of the exact-graph path: "auto", "cuda_cores" or "tensor_cores"."""
+    _check(lib.knn_exact_set_path(EXACT_PATHS[path]), "knn_exact_set_path")
+
+
+def knn_exact_last_info() -> dict:
+    """The calling thread's last exact build: path, n, rows redone by brute force, wait errors."""
+    info = KnnExactInfo()
+    _check(lib.knn_exact_last_info(ctypes.byref(info)), "knn_exact_last_info")
+    names = {v: k for k, v in EXACT_PATHS.items()}
+    return {"path": names.get(info.path, "none"), "n": info.n, "rows_redone": info.rows_redone,
+            "wait_errors": info.wait_errors}
 
 
 def knn_search_noalloc(rows, nbr_ids, queries, k_out: int, speedup: float, expansion: float,

@@ -102,6 +102,17 @@ def test_exact_graph_rejects_bad_sizes(knn):
     assert knn.lib.knn_exact_graph(X.ctypes.data, 5, 300, 2, ids.ctypes.data, None, None) == -7
 
 
+def test_exact_path_setting_checks_its_arguments(knn):
+    assert knn.lib.knn_exact_set_path(3) == -1
+    assert knn.lib.knn_exact_set_path(-1) == -1
+    assert knn.lib.knn_exact_last_info(None) == -1
+    for name in ("cuda_cores", "tensor_cores", "auto"):
+        knn.knn_exact_set_path(name)
+    assert ctypes.sizeof(knn.KnnExactInfo) == 24
+    info = knn.knn_exact_last_info()   # no build ran on this thread yet
+    assert info["n"] == 0 and info["rows_redone"] == 0
+
+
 def test_binding_raises_with_message(knn):
     with pytest.raises(knn.KnnError) as e:
         knn.knn_graph_create(_params(knn, k=0), np.zeros((20, 16), np.float32), stream=0)
