@@ -85,6 +85,8 @@ def _load():
                 "orc_exact_knn": (None, [_P, _I64, _I32, _I32, _P, _I64, _P, _P, _P, _P]),
                 "orc_search": (_I32, [_P, _I64, _I32, _P, _I32, _P, _P, _I32, _F64, _F64,
                                       _U64, _U64, _P, _I64, _P, _P, _P]),
+                "orc_search_climb": (_I32, [_P, _I64, _I32, _P, _I32, _P, _P, _I32, _F64, _F64,
+                                            _U64, _U64, _P, _I64, _I32, _P, _P, _P]),
                 "orc_rescore": (_I32, [_P, _I32, _P, _P, _I32, _I32, _P, _P, _P]),
                 "orc_update": (None, [_P, _I64, _I32, _P, _P, _I32, _P, _I64, _P, _P, _I32,
                                       _I32, _I32, _P]),
@@ -189,10 +191,16 @@ class SearchResult:
     margin: float
 
 
+CLIMBS = {"eager": 0, "best": 1}
+
+
 def search(X, nbr_ids, q, k_out: int, speedup: float, expansion: float,
            seed: int, stream: int, n: int | None = None, removed=None,
-           draws=None) -> SearchResult:
-    """iGNNS (Sec. 3) over the first n rows of X with adjacency nbr_ids [n, k]."""
+           draws=None, climb: str = "eager") -> SearchResult:
+    """iGNNS (Sec. 3) over the first n rows of X with adjacency nbr_ids [n, k].
+    climb="best" is the GNNS climb the paper compares against (every
+    unvisited neighbour evaluated, move to the most similar); use it with
+    expansion=inf for GNNS itself."""
     X = _f32(X)
     d = X.shape[1]
     n = X.shape[0] if n is None else n
@@ -203,10 +211,10 @@ def search(X, nbr_ids, q, k_out: int, speedup: float, expansion: float,
     sims = np.empty(k_out, np.float64)
     st = SearchStats()
     dr = None if draws is None else np.ascontiguousarray(draws, dtype=np.int64)
-    _load().orc_search(_ptr(X), n, d, _ptr(nbr), k, _ptr(_removed(removed, n)), _ptr(q),
-                       k_out, float(speedup), float(expansion), seed, stream,
-                       _ptr(dr), 0 if dr is None else dr.shape[0],
-                       _ptr(ids), _ptr(sims), ctypes.byref(st))
+    _load().orc_search_climb(_ptr(X), n, d, _ptr(nbr), k, _ptr(_removed(removed, n)), _ptr(q),
+                             k_out, float(speedup), float(expansion), seed, stream,
+                             _ptr(dr), 0 if dr is None else dr.shape[0], CLIMBS[climb],
+                             _ptr(ids), _ptr(sims), ctypes.byref(st))
     return SearchResult(ids, sims, st.evals, st.budget, st.restarts, st.discarded,
                         st.moves, st.draws, st.min_margin)
 
@@ -282,9 +290,9 @@ class Graph:
                                ("update_literal_evals", "i8"), ("search_margin", "f8"),
                                ("update_margin", "f8")])
 
-    def search(self, q, k_out, speedup, expansion, seed, stream) -> SearchResult:
+    def search(self, q, k_out, speedup, expansion, seed, stream, climb="eager") -> SearchResult:
         return search(self.X, self.ids[: self.n], q, k_out, speedup, expansion, seed,
-                      stream, n=self.n, removed=self.removed)
+                      stream, n=self.n, removed=self.removed, climb=climb)
 
 
 # --------------------------------------------------------------------------

@@ -16,6 +16,11 @@
  *   orc_search         -- iGNNS (Sec. 3): random restarts, the expansion test
  *                         sim(q,r) < s_max/e, eager hill climbing, and the
  *                         budget of n/speedup similarity computations.
+ *   orc_search_climb   -- the same search with a choice of climb: the eager
+ *                         rule of iGNNS, or the GNNS rule the paper compares
+ *                         against (Sec. 2.3, Sec. 3: every neighbour of the
+ *                         current node is evaluated and the search moves to
+ *                         the most similar one).
  *   orc_update         -- Update (Algorithm 2): walk from the found neighbours
  *                         to a fixed DEPTH and add `new` to lists "if needed".
  *   orc_insert_stream  -- the sequential online build (Algorithm 1), one new
@@ -53,6 +58,16 @@
  *   climb        neighbours of cur are scanned in stored (best-first) order;
  *                the first one whose similarity is strictly greater than
  *                sim(q, cur) becomes cur and the scan starts again.
+ *   GNNS climb   every unvisited neighbour of cur is evaluated (in stored
+ *                order, until the budget is spent); the most similar of
+ *                them (ties to the earlier position) becomes cur when it is
+ *                strictly more similar than cur.  Visited neighbours are
+ *                skipped as in iGNNS (no similarity is computed twice), and
+ *                the search runs on the same budget and restart draws, so
+ *                the two rules compare at equal evaluations.  Hajebi et
+ *                al.'s fixed restart count and depth cap are replaced by
+ *                that budget, and GNNS runs without the expansion test
+ *                (e = inf).
  *   update       level-1 sims are the ones the search returned (not counted
  *                again); lists are read before `new` is offered to them;
  *                the next level is the distinct ids gathered, minus nodes
@@ -241,6 +256,8 @@ typedef struct {
     double min_margin;  /* smallest relative margin of any decision            */
 } orc_search_stats;
 
+enum { ORC_CLIMB_EAGER = 0, ORC_CLIMB_BEST = 1 };
+
 static void note_margin(orc_search_stats *st, double m)
 {
     if (m < st->min_margin) st->min_margin = m;
@@ -256,12 +273,31 @@ static void note_margin(orc_search_stats *st, double m)
  *
  * Returns the number of results written (<= k_out), best first.
  */
+int32_t orc_search_climb(const float *X, int64_t n, int32_t d,
+                         const int64_t *nbr_ids, int32_t k, const uint8_t *removed,
+                         const float *q, int32_t k_out,
+                         double speedup, double expansion, uint64_t seed, uint64_t stream,
+                         const int64_t *draws, int64_t n_draws, int32_t climb,
+                         int64_t *out_ids, double *out_sims, orc_search_stats *st);
+
 int32_t orc_search(const float *X, int64_t n, int32_t d,
                    const int64_t *nbr_ids, int32_t k, const uint8_t *removed,
                    const float *q, int32_t k_out,
                    double speedup, double expansion, uint64_t seed, uint64_t stream,
                    const int64_t *draws, int64_t n_draws,
                    int64_t *out_ids, double *out_sims, orc_search_stats *st)
+{
+    return orc_search_climb(X, n, d, nbr_ids, k, removed, q, k_out, speedup, expansion, seed,
+                            stream, draws, n_draws, ORC_CLIMB_EAGER, out_ids, out_sims, st);
+}
+
+/* climb: ORC_CLIMB_EAGER (iGNNS) or ORC_CLIMB_BEST (GNNS). */
+int32_t orc_search_climb(const float *X, int64_t n, int32_t d,
+                         const int64_t *nbr_ids, int32_t k, const uint8_t *removed,
+                         const float *q, int32_t k_out,
+                         double speedup, double expansion, uint64_t seed, uint64_t stream,
+                         const int64_t *draws, int64_t n_draws, int32_t climb,
+                         int64_t *out_ids, double *out_sims, orc_search_stats *st)
 {
     memset(st, 0, sizeof(*st));
     st->min_margin = INFINITY;
@@ -320,11 +356,42 @@ int32_t orc_search(const float *X, int64_t n, int32_t d,
         }
         if (s > s_max) s_max = s;
 
-        /* eager hill climbing from r */
         int64_t cur = r;
         double s_cur = s;
         int moved = 1;
-        while (moved && !out_of_budget) {
+        /* GNNS hill climbing from r: evaluate every unvisited neighbour,
+         * then move to the most similar one if it beats cur */
+        while (climb == ORC_CLIMB_BEST && moved && !out_of_budget) {
+            moved = 0;
+            int64_t best = -1;
+            double s_best = -INFINITY;
+            for (int32_t i = 0; i < k; ++i) {
+                int64_t nb = nbr_ids[cur * k + i];
+                if (nb < 0 || visited[nb] || (removed && removed[nb])) continue;
+                if (st->evals == B) { out_of_budget = 1; break; }
+                double s_nb = similarity(q, X + nb * d, d);
+                st->evals++;
+                visited[nb] = 1;
+                n_visited++;
+                best_list_offer(&topk, s_nb, nb);
+                if (s_nb > s_max) s_max = s_nb;
+                if (best >= 0) note_margin(st, sim_gap(s_nb, s_best));
+                if (s_nb > s_best) {     /* ties keep the earlier position */
+                    best = nb;
+                    s_best = s_nb;
+                }
+            }
+            if (best < 0) break;         /* every neighbour visited: local maximum */
+            note_margin(st, sim_gap(s_best, s_cur));
+            if (s_best > s_cur) {
+                cur = best;
+                s_cur = s_best;
+                st->moves++;
+                moved = 1;
+            }
+        }
+        /* eager hill climbing from r */
+        while (climb == ORC_CLIMB_EAGER && moved && !out_of_budget) {
             moved = 0;
             for (int32_t i = 0; i < k; ++i) {
                 int64_t nb = nbr_ids[cur * k + i];

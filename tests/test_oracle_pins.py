@@ -150,15 +150,46 @@ def test_ignns_hand_trace_scan_order(orc):
         assert (r.evals, r.restarts, r.discarded, r.moves, r.draws) == tuple(int(v) for v in counts)
 
 
+def test_gnns_hand_trace(orc):
+    """GNNS climb (Sec. 2.3, Sec. 3) and the eager climb side by side on a
+    hand-traced six-point line."""
+    X = np.array([[10.0], [3.0], [1.0], [8.0], [9.0], [9.5]], np.float32)
+    nbr = np.array([[5, 1], [2, 3], [1, 3], [1, 4], [3, 5], [4, 0]], np.int64)
+    q = np.array([0.0], np.float32)
+    for ln in read_golden("gnns_line6.txt"):
+        head, draws, result, counts = (p.split() for p in ln.split("|"))
+        climb, speedup = head[1], float(head[2])
+        r = orc.search(X, nbr, q, 2, speedup, math.inf, seed=0, stream=0,
+                       draws=[int(v) for v in draws], climb=climb)
+        assert list(r.ids) == [int(v) for v in result], head[0]
+        assert (r.evals, r.restarts, r.discarded, r.moves, r.draws) == \
+            tuple(int(v) for v in counts), head[0]
+
+
+def test_gnns_spends_the_budget_and_moves_uphill(orc):
+    """On a mixture graph GNNS spends exactly B = floor(n / speedup)
+    evaluations (n_live > B), never discards (no expansion test), and returns
+    a sorted list."""
+    mix = Mixture(d=8, components=6, half_width=5.0, sigma=1.0, seed=4)
+    X = mix.sample(400, 1)
+    nbr, _, _ = orc.exact_knn(X, 8)
+    for i, q in enumerate(mix.sample(10, 2)):
+        for speedup in (4.0, 10.0):
+            r = orc.search(X, nbr, q, 5, speedup, math.inf, seed=3, stream=i, climb="best")
+            assert r.evals == math.floor(400 / speedup) and r.discarded == 0
+            assert np.all(np.diff(r.sims) <= 0)
+
+
 def test_ignns_exhaustive_special_case(orc):
     """speedup = 1 and no expansion test: every node is evaluated, so iGNNS is
-    linear search (Sec. 2.1) and returns the exact k nearest."""
+    linear search (Sec. 2.1) and returns the exact k nearest -- with either
+    climb."""
     mix = Mixture(d=8, components=5, half_width=5.0, sigma=1.0, seed=3)
     X = mix.sample(300, 1)
     nbr, _, _ = orc.exact_knn(X, 6)
     Q = mix.sample(20, 2)
     for i, q in enumerate(Q):
-        r = orc.search(X, nbr, q, 10, 1.0, math.inf, seed=9, stream=i)
+        r = orc.search(X, nbr, q, 10, 1.0, math.inf, seed=9, stream=i, climb="eager" if i % 2 else "best")
         sims = 1.0 / (1.0 + np.linalg.norm(X.astype(np.float64) - q.astype(np.float64), axis=1))
         expect = np.lexsort((np.arange(300), -sims))[:10]
         assert list(r.ids) == list(expect)
