@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--storage", default=None, choices=("fp32", "bf16", "fp8"),
                     help="searched copy of the rows (default: fp32; bf16 for precision)")
     ap.add_argument("--rescore-mult", type=int, default=4)
+    ap.add_argument("--experiment", default=None, choices=("search", "depth"),
+                    help="instead of the benchmark line: the search sweeps (expansion e; "
+                         "iGNNS against GNNS at equal evaluations) or the DEPTH sweep, "
+                         "one JSON line per point")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -320,11 +324,121 @@ def workload_config(args, W):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------
+# experiments (Sec. 8.2, 8.3): the paper's search and depth studies, on the
+# GPU path, against the exhaustive search of the same library
+# ---------------------------------------------------------------------------
+
+def _exp_line(**kv):
+    print(json.dumps(kv), flush=True)
+
+
+def run_search_experiment(knn, torch, np):
+    """Recall@10 of graph searches against exhaustive search (speedup 1, no
+    expansion test: linear search), on the exact 10-nn graph of each set.
+    (1) the expansion parameter e at a fixed speedup (the study behind the
+    paper's expansion figure: 5,000 synthetic points, speedup 50);
+    (2) iGNNS (eager climb + expansion test), GNNS (best-neighbour climb, no
+    test) and each improvement alone, at equal evaluations (the iGNNS/GNNS
+    comparison: 5,000 synthetic points, e = 5)."""
+    from paper_1602_06819_gb300 import inputs
+    sets = [
+        ("gmm-d3-n5000", inputs.Mixture(d=3, components=10, half_width=10.0, sigma=1.0, seed=41),
+         5000, 1000, 50.0, (2.0, 4.0, 8.0, 16.0, 32.0, 64.0, 128.0)),
+        ("gmm-d128-n100k", inputs.PLAIN_D128.mixture, 100000, 1024, 16.0,
+         (2.0, 4.0, 8.0, 16.0, 32.0, 64.0)),
+    ]
+    k = 10
+    for name, mix, n, nq, s_fixed, speedups in sets:
+        X = torch.from_numpy(mix.sample(n, 42)).cuda()
+        Q = torch.from_numpy(mix.sample(nq, 43)).cuda()
+        cfg = knn.GraphConfig(dim=mix.d, k=k, depth=2, speedup=1.0, expansion=math.inf,
+                              max_batch=nq, seed=7, capacity=n)
+        g = knn.Graph(cfg, X)
+        ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+        ctr = np.empty((nq, 8), np.int64)
+
+        def run(speedup, e, climb):
+            g.set_search(speedup, e, climb)
+            g.query(Q, k, 0, ids)
+            g.counters(ctr)
+            torch.cuda.synchronize()
+            return ids.clone(), float(ctr[:, 0].mean())
+
+        truth, ev_all = run(1.0, math.inf, "eager")
+
+        def recall(got):
+            return float((got[:, :, None] == truth[:, None, :]).any(-1).float().mean().item())
+
+        for e in (1.01, 1.2, 1.5, 2.0, 3.0, 5.0, 10.0, 20.0, math.inf):
+            got, ev = run(s_fixed, e, "eager")
+            _exp_line(experiment="expansion", set=name, n=n, queries=nq, k=k, speedup=s_fixed,
+                      expansion=None if math.isinf(e) else e, climb="eager", recall=recall(got),
+                      evals_per_query=ev)
+        for speedup in speedups:
+            for label, e, climb in (("iGNNS", 5.0, "eager"), ("GNNS", math.inf, "best"),
+                                    ("eager only", math.inf, "eager"), ("expansion only", 5.0, "best")):
+                got, ev = run(speedup, e, climb)
+                _exp_line(experiment="ignns_vs_gnns", set=name, n=n, queries=nq, k=k,
+                          speedup=speedup, method=label, expansion=None if math.isinf(e) else e,
+                          climb=climb, recall=recall(got), evals_per_query=ev)
+        g.close()
+
+
+def run_depth_experiment(knn, torch, np):
+    """The online build (Algorithm 1, one point at a time) with DEPTH 1..5:
+    edge recall and Q of the final graph against its exact graph, and the
+    similarities computed per insert (Sec. 8.3's depth study: 1,000 initial
+    synthetic points + 1,000 added at speedup 20; and 8,000 + 16,000 at
+    speedup 4)."""
+    from paper_1602_06819_gb300 import inputs
+    k = 10
+    runs = [("gmm-d16-1000+1000", inputs.SMALL_D16.mixture, 1000, 1000, 20.0),
+            ("gmm-d16-1000+1000", inputs.SMALL_D16.mixture, 1000, 1000, 4.0),
+            ("gmm-d16-8000+16000", inputs.SMALL_D16.mixture, 8000, 16000, 4.0)]
+    for name, mix, n0, na, speedup in runs:
+        X0 = torch.from_numpy(mix.sample(n0, 1)).cuda()
+        Xs = torch.from_numpy(mix.sample(na, 2)).cuda()
+        Xall = torch.cat([X0, Xs])
+        exact = torch.empty((n0 + na, k), dtype=torch.int64, device="cuda")
+        knn.knn_exact_graph(Xall, k, exact)
+        for depth in (1, 2, 3, 4, 5):
+            cfg = knn.GraphConfig(dim=mix.d, k=k, depth=depth, speedup=speedup, expansion=5.0,
+                                  max_batch=1, seed=4, capacity=n0 + na)
+            g = knn.Graph(cfg, X0)
+            st0 = g.stats()
+            t0 = time.perf_counter()
+            for i in range(na):
+                g.insert(Xs[i:i + 1])
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            st1 = g.stats()
+            online = torch.empty((n0 + na, k), dtype=torch.int64, device="cuda")
+            g.edges(online)
+            g.close()
+            e_c = edge_recall(torch, online, exact)
+            search = (st1["search_evals"] - st0["search_evals"]) / na
+            update = (st1["update_evals"] - st0["update_evals"]) / na
+            _exp_line(experiment="depth", set=name, n_init=n0, n_added=na, k=k, speedup=speedup,
+                      expansion=5.0, depth=depth, edge_recall=e_c / exact.numel(),
+                      Q=quality_q(e_c, n0, na, k), search_evals_per_insert=search,
+                      update_evals_per_insert=update, inserts_per_s=na / secs)
+
+
 def main():
     args = parse_args()
     W = pick_workload(args)
     if args.impl == "reference":
         run_reference(args, W)
+        return
+    if args.experiment:
+        import numpy as np
+        import torch
+        from paper_1602_06819_gb300 import build as kbuild
+        kbuild.build()
+        from paper_1602_06819_gb300 import knn
+        torch.cuda.set_device(0)
+        {"search": run_search_experiment, "depth": run_depth_experiment}[args.experiment](knn, torch, np)
         return
 
     import numpy as np

@@ -111,6 +111,15 @@ typedef enum knn_phase {
 
 typedef struct knn_graph knn_graph; /* opaque, owned by the library */
 
+/* Hill-climbing rule of a search (Sec. 3). */
+typedef enum knn_climb {
+    KNN_CLIMB_EAGER = 0, /* iGNNS: move to the first neighbour, in list order,
+                            strictly more similar than the current node      */
+    KNN_CLIMB_BEST = 1   /* GNNS (Sec. 2.3): evaluate every unvisited
+                            neighbour, move to the most similar one (ties to
+                            the earlier position) if it beats the current node */
+} knn_climb;
+
 /*
  * Create a graph from n_init >= k+1 points and build their exact k-nn graph
  * by brute force (Sec. 2.1; the initial graph of Sec. 8.5 is built the same
@@ -199,6 +208,17 @@ KNN_API knn_status knn_graph_set_timing(knn_graph *g, int32_t enable);
  * timing is off.
  */
 KNN_API knn_status knn_graph_last_timing(knn_graph *g, float *out_ms, int32_t n);
+
+/*
+ * Change the search parameters of a graph for its later inserts and queries:
+ * speedup (budget B = max(1, floor(n / speedup))), expansion e (<= 0 or
+ * +inf: no expansion test) and climb (knn_climb).  GNNS as the paper
+ * compares it with iGNNS is climb = KNN_CLIMB_BEST with expansion = +inf; it
+ * keeps iGNNS's budget, restart draws and visited set, so the two compare at
+ * equal similarity evaluations.  Errors: KNN_ERR_INVALID_ARG for a
+ * non-finite or non-positive speedup, a NaN expansion or an unknown climb.
+ */
+KNN_API knn_status knn_graph_set_search(knn_graph *g, double speedup, double expansion, int32_t climb);
 
 /* Running totals (synchronises the graph's last stream). */
 KNN_API knn_status knn_graph_stats(knn_graph *g, knn_stats *out);

@@ -70,6 +70,7 @@ struct knn_graph {
     cudaStream_t last_stream = nullptr;
     int64_t launches = 0;          // kernels launched by this library for the graph
     bool timing = false;           // record events around each phase
+    int32_t climb = KNN_CLIMB_EAGER;
     cudaEvent_t ev[KNN_NUM_PHASES + 1] = {};
     bool phase_ran[KNN_NUM_PHASES] = {};
 };
@@ -273,6 +274,7 @@ static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int 
     const double e = g->p.expansion;
     a.discard = (e > 0.0 && std::isfinite(e)) ? 1 : 0;
     a.expansion = a.discard ? (float)e : 1.0f;
+    a.climb = g->climb;
     CU(launch_search(g->p.storage, g->dp, a, s));
     ++g->launches;
     g->phase_ran[KNN_PHASE_SEARCH] = true;
@@ -817,6 +819,19 @@ KNN_API knn_status knn_exact_graph(const float *X, int64_t n, int32_t dim, int32
     for (void *p : {(void *)rows, (void *)ids, (void *)d2, (void *)xin, (void *)ids_tmp, (void *)sims_tmp})
         if (p) CU(cudaFreeAsync(p, s));
     if (ids_tmp || sims_tmp) CU(cudaStreamSynchronize(s));
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_set_search(knn_graph *g, double speedup, double expansion, int32_t climb) {
+    if (!g) return fail(KNN_ERR_INVALID_ARG, "null graph");
+    if (!(speedup > 0.0) || !std::isfinite(speedup))
+        return fail(KNN_ERR_INVALID_ARG, "speedup must be finite and > 0");
+    if (std::isnan(expansion)) return fail(KNN_ERR_INVALID_ARG, "expansion is NaN");
+    if (climb != KNN_CLIMB_EAGER && climb != KNN_CLIMB_BEST)
+        return fail(KNN_ERR_INVALID_ARG, "unknown climb %d", climb);
+    g->p.speedup = speedup;
+    g->p.expansion = expansion;
+    g->climb = climb;
     return KNN_OK;
 }
 

@@ -61,6 +61,7 @@ struct SearchArgs {
     uint64_t stream_base;        // restart stream of item i = stream_base + i
     float expansion;
     int32_t discard;             // expansion test enabled
+    int32_t climb;               // KNN_CLIMB_EAGER (iGNNS) or KNN_CLIMB_BEST (GNNS)
 };
 
 struct RescoreArgs {

@@ -23,7 +23,10 @@
 // * Climbs.  A step gathers the rows of all neighbours of the current node in
 //   the same round trip as their visited bits; one ballot then finds the
 //   first unvisited neighbour (in list order) that is strictly more similar,
-//   and every unvisited neighbour up to it is committed.
+//   and every unvisited neighbour up to it is committed.  The GNNS climb the
+//   paper compares against (Sec. 2.3) commits every unvisited neighbour and
+//   moves to the most similar one (a warp minimum) when it beats the
+//   current node.
 //
 // Visited sets.  A query's bitset lives in shared memory when the bitsets of
 // a block's warps fit two blocks on an SM (about 220,000 nodes); marks are
@@ -237,9 +240,27 @@ ignns_search_kernel(const SearchArgs a) {
                     unsigned um = __ballot_sync(FULL, valid && !seen);
                     if (um == 0u) break;  // every neighbour visited: local maximum
                     um = lowest_bits(um, limit - evals);
-                    const unsigned better = um & __ballot_sync(FULL, nd2 < d2cur);
-                    const int mi = better ? __ffs(better) - 1 : 32;
-                    const unsigned evc = mi < 32 ? (um & upto(mi)) : um;
+                    int mi;
+                    unsigned evc;
+                    if (a.climb == KNN_CLIMB_BEST) {
+                        // GNNS: every unvisited neighbour is evaluated; the
+                        // most similar (ties to the earlier position) becomes
+                        // cur if it is strictly more similar than cur
+                        evc = um;
+                        uint64_t pk = ((evc >> lane) & 1u)
+                                          ? (((uint64_t)__float_as_uint(nd2) << 32) | (uint32_t)lane)
+                                          : ~0ull;
+#pragma unroll
+                        for (int off = 16; off >= 1; off >>= 1) {
+                            const uint64_t o = shfl_u64_xor(pk, off);
+                            pk = o < pk ? o : pk;
+                        }
+                        mi = __uint_as_float((uint32_t)(pk >> 32)) < d2cur ? (int)(uint32_t)pk : 32;
+                    } else {
+                        const unsigned better = um & __ballot_sync(FULL, nd2 < d2cur);
+                        mi = better ? __ffs(better) - 1 : 32;
+                        evc = mi < 32 ? (um & upto(mi)) : um;
+                    }
                     evals += __popc(evc);
                     const bool mine = (evc >> lane) & 1u;
                     if (mine) vis.mark((uint32_t)nb);

@@ -31,6 +31,10 @@ KNN_ERR_DEVICE_TIMEOUT = -5
 KNN_ERR_NOT_FOUND = -6
 KNN_ERR_UNSUPPORTED = -7
 
+KNN_CLIMB_EAGER = 0
+KNN_CLIMB_BEST = 1
+CLIMBS = {"eager": KNN_CLIMB_EAGER, "best": KNN_CLIMB_BEST}
+
 KNN_STORAGE_FP32 = 0
 KNN_STORAGE_BF16 = 1
 KNN_STORAGE_FP8_E4M3 = 2
@@ -42,7 +46,7 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
 # Every symbol include/knn_graph.h declares.
 EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
             "knn_graph_remove", "knn_graph_get_edges", "knn_graph_last_counters",
-            "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_stats",
+            "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
             "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
             "knn_search_noalloc", "knn_last_error", "knn_version")
 
@@ -100,6 +104,7 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_destroy": (None, [P]),
         "knn_exact_graph": (I32, [P, I64, I32, I32, P, P, P]),
         "knn_exact_set_path": (I32, [I32]),
+        "knn_graph_set_search": (I32, [P, ctypes.c_double, ctypes.c_double, I32]),
         "knn_exact_last_info": (I32, [ctypes.POINTER(KnnExactInfo)]),
         "knn_search_noalloc": (I32, [P, I64, I32, P, I32, P, I64, I32, ctypes.c_double,
                                      ctypes.c_double, U64, U64, P, P, P]),
@@ -205,6 +210,13 @@ def knn_graph_last_counters(g, out, stream=None) -> None:
     _check_dtype(out, "int64", "out")
     _check(lib.knn_graph_last_counters(g, _ptr(out), out.shape[0], _stream(stream)),
            "knn_graph_last_counters")
+
+
+def knn_graph_set_search(handle, speedup: float, expansion: float, climb: str = "eager") -> None:
+    """Search parameters of later inserts and queries; climb "eager" (iGNNS)
+    or "best" (GNNS, with expansion=inf as the paper compares it)."""
+    _check(lib.knn_graph_set_search(handle, float(speedup), float(expansion), CLIMBS[climb]),
+           "knn_graph_set_search")
 
 
 def knn_graph_set_timing(g, enable: bool) -> None:
@@ -321,6 +333,9 @@ class Graph:
 
     def set_timing(self, enable: bool = True):
         knn_graph_set_timing(self.handle, enable)
+
+    def set_search(self, speedup: float, expansion: float, climb: str = "eager"):
+        knn_graph_set_search(self.handle, speedup, expansion, climb)
 
     def last_timing(self) -> dict:
         return knn_graph_last_timing(self.handle)

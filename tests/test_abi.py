@@ -113,6 +113,10 @@ def test_exact_path_setting_checks_its_arguments(knn):
     assert info["n"] == 0 and info["rows_redone"] == 0
 
 
+def test_set_search_checks_its_arguments(knn):
+    assert knn.lib.knn_graph_set_search(None, 4.0, 5.0, 0) == -1
+
+
 def test_binding_raises_with_message(knn):
     with pytest.raises(knn.KnnError) as e:
         knn.knn_graph_create(_params(knn, k=0), np.zeros((20, 16), np.float32), stream=0)

@@ -2,8 +2,8 @@
 for every query whose decisions all have a margin above the FP32 tolerance,
 the ids, the similarity count (the budget), the restarts, discards, moves and
 draws must be identical.  Covers the FP32, BF16 and FP8-E4M3 searched copies
-(FP32 re-score of the best candidates), removed nodes and the exhaustive
-special case."""
+(FP32 re-score of the best candidates), removed nodes, the exhaustive
+special case and the GNNS climb the paper compares against."""
 import math
 
 import numpy as np
@@ -55,11 +55,13 @@ def run_queries(g, Q, k_out, qid0):
 
 
 def compare(knn, X0, Q, k, k_out, speedup, e, seed, storage=0, rescore_mult=4, removed=None,
-            max_ambiguous=0.4):
+            max_ambiguous=0.4, climb="eager"):
     n, d = X0.shape
     o_ids, _, _ = oracle.exact_knn(X0, k)
     g = make_graph(knn, X0, k, speedup, e, seed, storage, rescore_mult, nbr_ids=o_ids)
     try:
+        if climb != "eager":
+            g.set_search(speedup, e, climb)
         assert np.array_equal(graph_edges(g, n, k), o_ids), "restored lists differ"
         rem = None
         if removed is not None:
@@ -81,7 +83,8 @@ def compare(knn, X0, Q, k, k_out, speedup, e, seed, storage=0, rescore_mult=4, r
     ambiguous = 0
     for i, q in enumerate(Q):
         kt = k_out if storage == 0 else rescore_mult * k_out
-        r = oracle.search(Xs, o_ids, q, kt, speedup, e, seed, (1 << 63) + qid0 + i, removed=rem)
+        r = oracle.search(Xs, o_ids, q, kt, speedup, e, seed, (1 << 63) + qid0 + i, removed=rem,
+                          climb=climb)
         margin = r.margin
         exp_ids, exp_sims = r.ids, r.sims
         if storage != 0:
@@ -106,6 +109,41 @@ def test_queries_small_d16(knn, speedup, e):
     mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=11)
     X0, Q = mix.sample(1000, 1), mix.sample(96, 3)
     compare(knn, X0, Q, 10, 10, speedup, e, seed=4)
+
+
+@pytest.mark.parametrize("d,speedup,e", [(16, 4.0, math.inf), (16, 20.0, math.inf), (16, 8.0, 5.0),
+                                         (128, 4.0, math.inf)])
+def test_queries_gnns_climb(knn, d, speedup, e):
+    """GNNS (Sec. 2.3): every unvisited neighbour evaluated, move to the most
+    similar; with and without the expansion test."""
+    mix = Mixture(d=d, components=10, half_width=10.0 if d == 16 else 20.0, sigma=1.0, seed=11)
+    X0, Q = mix.sample(1000 if d == 16 else 3000, 1), mix.sample(96, 3)
+    compare(knn, X0, Q, 10, 10, speedup, e, seed=4, climb="best", max_ambiguous=0.6)
+
+
+def test_queries_gnns_climb_screened_and_removed(knn):
+    mix = Mixture(d=32, components=8, half_width=10.0, sigma=1.0, seed=5)
+    X0, Q = mix.sample(1500, 1), mix.sample(64, 3)
+    removed = np.random.default_rng(3).choice(1500, 60, replace=False)
+    compare(knn, X0, Q, 8, 8, 4.0, math.inf, seed=2, storage=1, removed=removed, climb="best",
+            max_ambiguous=0.6)
+
+
+def test_set_search_changes_parameters(knn):
+    """Search parameters changed on a live graph take effect on the next
+    call: the budget follows the new speedup."""
+    mix = Mixture(d=16, components=4, half_width=10.0, sigma=1.0, seed=6)
+    X0, Q = mix.sample(600, 1), mix.sample(8, 2)
+    g = make_graph(knn, X0, 8, 4.0, 5.0, seed=1)
+    try:
+        _, _, c1 = run_queries(g, Q, 5, 0)
+        g.set_search(10.0, math.inf, "best")
+        _, _, c2 = run_queries(g, Q, 5, 0)
+        with pytest.raises(knn.KnnError):
+            g.set_search(0.0, 5.0, "eager")
+    finally:
+        g.close()
+    assert np.all(c1[:, 0] == 150) and np.all(c2[:, 0] == 60) and np.all(c2[:, 3] == 0)
 
 
 def test_queries_d128_many_tiles(knn):
