@@ -87,6 +87,10 @@ def _load():
                                       _U64, _U64, _P, _I64, _P, _P, _P]),
                 "orc_search_climb": (_I32, [_P, _I64, _I32, _P, _I32, _P, _P, _I32, _F64, _F64,
                                             _U64, _U64, _P, _I64, _I32, _P, _P, _P]),
+                "orc_kmedoids_init": (None, [_I64, _I32, _U64, _P]),
+                "orc_kmedoids_assign": (None, [_P, _I64, _I32, _P, _I32, _F64, _I32, _P, _P]),
+                "orc_kmedoids_medoid": (_I64, [_P, _I32, _P, _I64, _P]),
+                "orc_kmedoids": (None, [_P, _I64, _I32, _I32, _F64, _I32, _I32, _U64, _P, _P, _P]),
                 "orc_rescore": (_I32, [_P, _I32, _P, _P, _I32, _I32, _P, _P, _P]),
                 "orc_update": (None, [_P, _I64, _I32, _P, _P, _I32, _P, _I64, _P, _P, _I32,
                                       _I32, _I32, _P]),
@@ -217,6 +221,51 @@ def search(X, nbr_ids, q, k_out: int, speedup: float, expansion: float,
                              _ptr(ids), _ptr(sims), ctypes.byref(st))
     return SearchResult(ids, sims, st.evals, st.budget, st.restarts, st.discarded,
                         st.moves, st.draws, st.min_margin)
+
+
+# --------------------------------------------------------------------------
+# balanced k-medoids (Sec. 7, Algorithm 4)
+# --------------------------------------------------------------------------
+
+def kmedoids_init(n: int, p: int, seed: int) -> np.ndarray:
+    """p distinct initial medoids drawn with the restart generator."""
+    out = np.empty(p, np.int64)
+    _load().orc_kmedoids_init(n, p, seed, _ptr(out))
+    return out
+
+
+def kmedoids_assign(X, medoids, imbalance: float, chunks: int):
+    """Assign step with the capacity penalty w(t, m): (labels int32 [n],
+    margins float64 [n])."""
+    X = _f32(X)
+    n, d = X.shape
+    med = np.ascontiguousarray(medoids, dtype=np.int64)
+    labels = np.empty(n, np.int32)
+    margins = np.empty(n, np.float64)
+    _load().orc_kmedoids_assign(_ptr(X), n, d, _ptr(med), med.shape[0], float(imbalance), chunks,
+                                _ptr(labels), _ptr(margins))
+    return labels, margins
+
+
+def kmedoids_medoid(X, members):
+    """Update step of one cluster: (medoid id, margin)."""
+    X = _f32(X)
+    mem = np.ascontiguousarray(members, dtype=np.int64)
+    g = ctypes.c_double()
+    m = _load().orc_kmedoids_medoid(_ptr(X), X.shape[1], _ptr(mem), mem.shape[0], ctypes.byref(g))
+    return int(m), g.value
+
+
+def kmedoids(X, p: int, imbalance: float, chunks: int, iters: int, seed: int):
+    """Algorithm 4: (labels int32 [n], medoids int64 [p], smallest margin)."""
+    X = _f32(X)
+    n, d = X.shape
+    labels = np.empty(n, np.int32)
+    med = np.empty(p, np.int64)
+    g = ctypes.c_double()
+    _load().orc_kmedoids(_ptr(X), n, d, p, float(imbalance), chunks, iters, seed, _ptr(labels),
+                         _ptr(med), ctypes.byref(g))
+    return labels, med, g.value
 
 
 def rescore(X, q, cand_ids, k_out: int):

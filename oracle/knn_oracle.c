@@ -28,6 +28,9 @@
  *   orc_rescore        -- exact re-scoring of screening candidates (the
  *                         reduced-precision storage forms; the paper fixes no
  *                         precision, so the exact form is FP64 here).
+ *   orc_kmedoids_*     -- balanced k-medoids (Sec. 7, Algorithm 4): the
+ *                         weighted assign step with the capacity penalty
+ *                         w(t, m), the medoid update, and their iteration.
  *   orc_correct_edges  -- correct edges e_c of an online graph (Sec. 8.5).
  *   orc_quality_q      -- Q = (e_c - e_u)/e_m with e_m, e_u of Sec. 8.5.
  *   orc_quantize_*     -- BF16 and FP8-E4M3 storage codes from their bit-level
@@ -755,4 +758,135 @@ void orc_quantize_e4m3(const float *X, int64_t n, int32_t d,
             deq[r * d + i] = back;
         }
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Balanced k-medoids (Sec. 7, Algorithm 4).                                 */
+/*                                                                           */
+/* The paper partitions a graph for its distributed search with a balanced   */
+/* k-medoids clustering: p initial medoids drawn at random; the data spread */
+/* over c compute nodes; each compute node assigns its points, one after    */
+/* the other, to the medoid m that maximises sim(m, x) * w(t, m) with        */
+/*   w(t, m) = 1 - |C_t(m)| / capacity,  capacity = n * imbalance / (p * c), */
+/* |C_t(m)| counting the points that compute node has given m so far; then  */
+/* every cluster takes as new medoid the member with the smallest sum of     */
+/* distances to the other members, and the two steps repeat.                */
+/*                                                                           */
+/* Readings: the c "compute nodes" are c chunks of consecutive ids,          */
+/* chunk j = [floor(j n / c), floor((j+1) n / c)) (the input order of the   */
+/* synthetic data is random, so this is a random split), each assigned in   */
+/* id order; the clusters are ordered by medoid position and an argmax tie  */
+/* goes to the lower position; the distance of the update step is the       */
+/* Euclidean distance (the paper's Spark version measures shortest paths in */
+/* the graph there, and the Euclidean similarity in the assign step); an    */
+/* empty cluster keeps its medoid; an update tie goes to the lower id.      */
+/* The initial medoids are the first p distinct nodes drawn with the        */
+/* restart generator keyed (seed, stream 2^62).                             */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_KMEDOIDS_STREAM (1ULL << 62)
+
+/* p distinct initial medoids (p <= n). */
+void orc_kmedoids_init(int64_t n, int32_t p, uint64_t seed, int64_t *medoids)
+{
+    uint64_t key = orc_search_key(seed, ORC_KMEDOIDS_STREAM);
+    uint8_t *taken = (uint8_t *)calloc((size_t)n, 1);
+    int32_t got = 0;
+    for (uint64_t j = 0; got < p; ++j) {
+        int64_t r = orc_draw(key, j, n);
+        if (taken[r]) continue;
+        taken[r] = 1;
+        medoids[got++] = r;
+    }
+    free(taken);
+}
+
+/* Assign step.  labels[i] = cluster (medoid position) of node i; margins[i]
+ * (nullable) = relative gap between the best and second-best weighted
+ * similarity of that decision. */
+void orc_kmedoids_assign(const float *X, int64_t n, int32_t d, const int64_t *medoids, int32_t p,
+                         double imbalance, int32_t chunks, int32_t *labels, double *margins)
+{
+    double capacity = (double)n * imbalance / ((double)p * (double)chunks);
+    int64_t *count = (int64_t *)malloc(sizeof(int64_t) * (size_t)p);
+    for (int32_t c = 0; c < chunks; ++c) {
+        int64_t lo = (int64_t)(((__int128)c * n) / chunks);
+        int64_t hi = (int64_t)(((__int128)(c + 1) * n) / chunks);
+        for (int32_t m = 0; m < p; ++m) count[m] = 0;
+        for (int64_t i = lo; i < hi; ++i) {
+            int32_t best = -1;
+            double s_best = -INFINITY, s_second = -INFINITY;
+            for (int32_t m = 0; m < p; ++m) {
+                double w = 1.0 - (double)count[m] / capacity;
+                double score = similarity(X + i * d, X + medoids[m] * d, d) * w;
+                if (score > s_best) {
+                    s_second = s_best;
+                    s_best = score;
+                    best = m;
+                } else if (score > s_second) {
+                    s_second = score;
+                }
+            }
+            labels[i] = best;
+            count[best]++;
+            if (margins) margins[i] = p > 1 ? rel_gap(s_best, s_second) : INFINITY;
+        }
+    }
+    free(count);
+}
+
+/* Update step for one cluster: the member (ids `members`, cnt >= 1) whose sum
+ * of Euclidean distances to the other members is smallest, ties to the lower
+ * id; *margin = relative gap to the runner-up (inf for one member). */
+int64_t orc_kmedoids_medoid(const float *X, int32_t d, const int64_t *members, int64_t cnt,
+                            double *margin)
+{
+    int64_t best = -1;
+    double s_best = INFINITY, s_second = INFINITY;
+    for (int64_t a = 0; a < cnt; ++a) {
+        double sum = 0.0;
+        for (int64_t b = 0; b < cnt; ++b)
+            sum += sqrt(squared_l2(X + members[a] * d, X + members[b] * d, d));
+        int64_t id = members[a];
+        if (sum < s_best || (sum == s_best && id < best)) {
+            s_second = s_best;
+            s_best = sum;
+            best = id;
+        } else if (sum < s_second) {
+            s_second = sum;
+        }
+    }
+    if (margin) *margin = cnt > 1 ? rel_gap(s_best, s_second) : INFINITY;
+    return best;
+}
+
+/* Algorithm 4: `iters` rounds of (assign, update), then a final assign.
+ * labels [n]; medoids [p] (those of the final assign); *min_margin = the
+ * smallest decision margin of the whole run. */
+void orc_kmedoids(const float *X, int64_t n, int32_t d, int32_t p, double imbalance,
+                  int32_t chunks, int32_t iters, uint64_t seed, int32_t *labels, int64_t *medoids,
+                  double *min_margin)
+{
+    double *margins = (double *)malloc(sizeof(double) * (size_t)n);
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    double mm = INFINITY;
+    orc_kmedoids_init(n, p, seed, medoids);
+    for (int32_t it = 0; ; ++it) {
+        orc_kmedoids_assign(X, n, d, medoids, p, imbalance, chunks, labels, margins);
+        for (int64_t i = 0; i < n; ++i)
+            if (margins[i] < mm) mm = margins[i];
+        if (it == iters) break;
+        for (int32_t m = 0; m < p; ++m) {
+            int64_t cnt = 0;
+            for (int64_t i = 0; i < n; ++i)
+                if (labels[i] == m) members[cnt++] = i;
+            if (cnt == 0) continue;
+            double g;
+            medoids[m] = orc_kmedoids_medoid(X, d, members, cnt, &g);
+            if (g < mm) mm = g;
+        }
+    }
+    if (min_margin) *min_margin = mm;
+    free(margins);
+    free(members);
 }

@@ -441,3 +441,66 @@ def test_e4m3_rowwise_scale(orc):
     # relative error of E4M3 is at most 2^-4 of the value (3 mantissa bits)
     big = np.abs(X) > scales[:, None] * 2.0**-6
     assert np.all(np.abs(deq - X)[big] <= np.abs(X)[big] * 2.0**-4 * 1.0001)
+
+
+# ---------------------------------------------------------------------------
+# balanced k-medoids (Sec. 7, Algorithm 4)
+# ---------------------------------------------------------------------------
+
+def test_kmedoids_hand_trace(orc):
+    X = np.array([[0.0], [1.0], [2.0], [10.0]], np.float32)
+    for ln in read_golden("kmedoids_line4.txt"):
+        step, med, imb, want = (p.split() for p in ln.split("|"))
+        med = [int(v) for v in med]
+        imb = float(imb[0])
+        labels, _ = orc.kmedoids_assign(X, med, imb, 1)
+        if step[0] == "assign":
+            assert labels.tolist() == [int(v) for v in want]
+        else:
+            new = [orc.kmedoids_medoid(X, np.flatnonzero(labels == m))[0] for m in range(len(med))]
+            assert new == [int(v) for v in want]
+
+
+def test_kmedoids_without_penalty_is_nearest_medoid(orc):
+    """imbalance = inf makes w = 1: each point goes to its most similar
+    medoid, i.e. the nearest one (checked against a direct argmin)."""
+    mix = Mixture(d=6, components=5, half_width=5.0, sigma=1.0, seed=8)
+    X = mix.sample(500, 1)
+    med = orc.kmedoids_init(500, 12, seed=3)
+    labels, margins = orc.kmedoids_assign(X, med, math.inf, 4)
+    D = np.linalg.norm(X.astype(np.float64)[:, None, :] - X.astype(np.float64)[med][None], axis=2)
+    safe = margins > 1e-12
+    assert np.array_equal(labels[safe], np.argmin(D, axis=1)[safe])
+
+
+def test_kmedoids_balance_and_medoid_definition(orc):
+    """With imbalance 1.1 no cluster takes more than ceil(capacity) points of
+    a chunk; each medoid the update picks minimises the sum of distances to
+    its cluster (checked by brute force); the init draws are distinct."""
+    mix = Mixture(d=4, components=3, half_width=5.0, sigma=1.0, seed=9)
+    n, p, c = 1200, 8, 3
+    X = mix.sample(n, 1)
+    med = orc.kmedoids_init(n, p, seed=5)
+    assert len(set(med.tolist())) == p and med.min() >= 0 and med.max() < n
+    labels, _ = orc.kmedoids_assign(X, med, 1.1, c)
+    cap = n * 1.1 / (p * c)
+    for j in range(c):
+        lo, hi = j * n // c, (j + 1) * n // c
+        assert np.bincount(labels[lo:hi], minlength=p).max() <= math.ceil(cap)
+    Xd = X.astype(np.float64)
+    for m in range(p):
+        mem = np.flatnonzero(labels == m)
+        got, _ = orc.kmedoids_medoid(X, mem)
+        sums = np.linalg.norm(Xd[mem][:, None] - Xd[mem][None], axis=2).sum(1)
+        assert got == mem[np.argmin(sums)]
+
+
+def test_kmedoids_iterations(orc):
+    """The whole loop: labels use the returned medoids (re-assigning with
+    them reproduces the labels), and every cluster is non-empty."""
+    mix = Mixture(d=4, components=6, half_width=8.0, sigma=1.0, seed=2)
+    X = mix.sample(900, 1)
+    labels, med, _ = orc.kmedoids(X, 6, 1.2, 3, 2, seed=11)
+    again, _ = orc.kmedoids_assign(X, med, 1.2, 3)
+    assert np.array_equal(labels, again)
+    assert np.bincount(labels, minlength=6).min() > 0
