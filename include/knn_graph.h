@@ -303,6 +303,36 @@ KNN_API knn_status knn_search_noalloc(const float *rows, int64_t n, int32_t dim,
                                       uint64_t seed, uint64_t query_id0, int64_t *out_ids,
                                       float *out_sims, void *stream);
 
+/*
+ * Balanced k-medoids (Sec. 7, Algorithm 4) of n points, for a node ordering
+ * that makes clusters contiguous and for the partitions of the partitioned
+ * search (Algorithm 3, knn_graph_query_partitioned).
+ *
+ * X: [n, dim] float32, host or device; 1 <= dim <= 256.  p clusters,
+ * 1 <= p <= 1024, p <= n < 2^31, n * p <= 2^32.  The initial medoids are the
+ * first p distinct nodes drawn with the restart generator keyed
+ * (seed, 2^62).  The points are split in `chunks` chunks of consecutive ids
+ * (the paper's compute nodes, 1 <= chunks <= n); within a chunk, in id
+ * order, a point goes to the medoid m maximising sim(m, x) * w(t, m) with
+ * w(t, m) = 1 - |C_t(m)| / capacity, capacity = n * imbalance / (p * chunks)
+ * and |C_t(m)| the chunk's points given to m so far (ties to the lower
+ * cluster); imbalance >= 1, +inf for no penalty.  `iters` rounds of (assign,
+ * update) run before the final assign, the update giving every non-empty
+ * cluster its member with the smallest sum of Euclidean distances to the
+ * others (ties to the lower id).  Decisions are taken in FP32.
+ *
+ * Outputs (each nullable, host or device): labels [n] int32 (cluster of each
+ * point); medoids [p] int64 (those of the final assign); order [n] int64
+ * (point ids sorted by (cluster, id): position -> point); offsets [p + 1]
+ * int64 (cluster m occupies order[offsets[m] .. offsets[m+1])).  Allocates
+ * n * (p + dim + 4) * 4 bytes of temporaries and returns when the outputs
+ * are written.
+ */
+KNN_API knn_status knn_balanced_kmedoids(const float *X, int64_t n, int32_t dim, int32_t p,
+                                         double imbalance, int32_t chunks, int32_t iters,
+                                         uint64_t seed, int32_t *out_labels, int64_t *out_medoids,
+                                         int64_t *out_order, int64_t *out_offsets, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 KNN_API const char *knn_last_error(void);
 

@@ -24,19 +24,23 @@ enum Storage : int { ST_FP32 = 0, ST_BF16 = 1, ST_FP8 = 2 };
 // the generator seeded with v; draw j picks node floor(x_j * n / 2^64)
 // (Lemire's multiply-shift range reduction).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t splitmix_fin(uint64_t z) {
+__host__ __device__ __forceinline__ uint64_t splitmix_fin(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
-__device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t j) {
+__host__ __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t j) {
     return splitmix_fin(seed + (j + 1ull) * 0x9E3779B97F4A7C15ull);
 }
-__device__ __forceinline__ uint64_t restart_key(uint64_t seed, uint64_t stream) {
+__host__ __device__ __forceinline__ uint64_t restart_key(uint64_t seed, uint64_t stream) {
     return splitmix_out(seed ^ splitmix_out(stream, 0), 0);
 }
-__device__ __forceinline__ uint32_t restart_node(uint64_t key, uint64_t j, uint32_t n) {
+__host__ __device__ __forceinline__ uint32_t restart_node(uint64_t key, uint64_t j, uint32_t n) {
+#ifdef __CUDA_ARCH__
     return (uint32_t)__umul64hi(splitmix_out(key, j), (uint64_t)n);
+#else
+    return (uint32_t)(((unsigned __int128)splitmix_out(key, j) * (uint64_t)n) >> 64);
+#endif
 }
 
 // ---------------------------------------------------------------------------

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "knn_graph.h"
+#include "common.cuh"
 #include "kernels.h"
 
 using namespace knn;
@@ -832,6 +833,83 @@ KNN_API knn_status knn_graph_set_search(knn_graph *g, double speedup, double exp
     g->p.speedup = speedup;
     g->p.expansion = expansion;
     g->climb = climb;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_balanced_kmedoids(const float *X, int64_t n, int32_t dim, int32_t p,
+                                         double imbalance, int32_t chunks, int32_t iters,
+                                         uint64_t seed, int32_t *out_labels, int64_t *out_medoids,
+                                         int64_t *out_order, int64_t *out_offsets, void *stream) {
+    if (!X) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (dim < 1 || dim > 256) return fail(KNN_ERR_UNSUPPORTED, "dim %d outside 1..256", dim);
+    if (p < 1 || p > KMED_MAX_P) return fail(KNN_ERR_UNSUPPORTED, "p %d outside 1..%d", p, KMED_MAX_P);
+    if (n < p || n >= (int64_t)INT32_MAX) return fail(KNN_ERR_INVALID_ARG, "need p <= n < 2^31");
+    if ((double)n * (double)p > 4294967296.0)
+        return fail(KNN_ERR_UNSUPPORTED, "n * p above 2^32 (the point-medoid distance matrix)");
+    if (!(imbalance >= 1.0)) return fail(KNN_ERR_INVALID_ARG, "imbalance must be >= 1");
+    if (chunks < 1 || chunks > n) return fail(KNN_ERR_INVALID_ARG, "chunks %d outside 1..n", chunks);
+    if (iters < 0 || iters > 1000) return fail(KNN_ERR_INVALID_ARG, "iters %d outside 0..1000", iters);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int dp = padded_dim(dim);
+    // initial medoids: the first p distinct draws of the generator keyed (seed, 2^62)
+    std::vector<int64_t> med0((size_t)p);
+    {
+        std::vector<char> taken((size_t)n, 0);
+        const uint64_t key = restart_key(seed, 1ull << 62);
+        int got = 0;
+        for (uint64_t j = 0; got < p; ++j) {
+            const uint32_t r = restart_node(key, j, (uint32_t)n);
+            if (taken[r]) continue;
+            taken[r] = 1;
+            med0[(size_t)got++] = r;
+        }
+    }
+    float *rows = nullptr, *D = nullptr, *xin = nullptr;
+    int32_t *labels = nullptr;
+    int64_t *medoids = nullptr, *order = nullptr, *offsets = nullptr;
+    void *sort_scratch = nullptr;
+    auto release = [&]() {
+        for (void *q : {(void *)rows, (void *)D, (void *)xin, (void *)labels, (void *)medoids, (void *)order,
+                        (void *)offsets, sort_scratch})
+            if (q) cudaFreeAsync(q, s);
+    };
+    auto run = [&]() -> knn_status {
+        CU(cudaMallocAsync(&rows, (size_t)n * dp * 4, s));
+        CU(cudaMallocAsync(&D, (size_t)n * p * 4, s));
+        CU(cudaMallocAsync(&labels, (size_t)n * 4, s));
+        CU(cudaMallocAsync(&medoids, (size_t)p * 8, s));
+        CU(cudaMallocAsync(&order, (size_t)n * 8, s));
+        CU(cudaMallocAsync(&offsets, (size_t)(p + 1) * 8, s));
+        CU(cudaMallocAsync(&sort_scratch, kmed_sort_scratch_bytes(n, p), s));
+        const bool x_dev = is_device_ptr(X);
+        if (!x_dev) {
+            CU(cudaMallocAsync(&xin, (size_t)n * dim * 4, s));
+            CU(cudaMemcpyAsync(xin, X, (size_t)n * dim * 4, cudaMemcpyHostToDevice, s));
+        }
+        CU(launch_append(x_dev ? X : xin, n, dim, dp, rows, nullptr, nullptr, nullptr, s));
+        CU(cudaMemcpyAsync(medoids, med0.data(), (size_t)p * 8, cudaMemcpyHostToDevice, s));
+        const double capacity = (double)n * imbalance / ((double)p * (double)chunks);
+        for (int it = 0;; ++it) {
+            CU(launch_kmed_dist(dp, rows, n, medoids, p, D, s));
+            CU(launch_kmed_assign(D, n, p, chunks, capacity, labels, s));
+            CU(launch_kmed_sort(labels, n, p, sort_scratch, order, offsets, s));
+            if (it == iters) break;
+            CU(launch_kmed_update(dp, rows, order, offsets, p, medoids, s));
+        }
+        auto out = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+            if (!dst) return cudaSuccess;
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+        };
+        CU(out(out_labels, labels, (size_t)n * 4));
+        CU(out(out_medoids, medoids, (size_t)p * 8));
+        CU(out(out_order, order, (size_t)n * 8));
+        CU(out(out_offsets, offsets, (size_t)(p + 1) * 8));
+        return KNN_OK;
+    };
+    const knn_status st = run();
+    release();
+    if (st != KNN_OK) return st;
+    CU(cudaStreamSynchronize(s));
     return KNN_OK;
 }
 

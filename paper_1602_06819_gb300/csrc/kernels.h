@@ -168,6 +168,22 @@ cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned 
 cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,
                                  int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s);
 
+// balanced k-medoids (kmedoids.cu); X are padded FP32 rows [n][dp]
+constexpr int KMED_MAX_P = 1024;
+// D[i][m] = squared distance of point i to medoid m ([n][p] floats)
+cudaError_t launch_kmed_dist(int dp, const float *X, int64_t n, const int64_t *medoids, int p, float *D,
+                             cudaStream_t s);
+// the sequential weighted assignment, one warp per chunk of consecutive ids
+cudaError_t launch_kmed_assign(const float *D, int64_t n, int p, int chunks, double capacity, int32_t *labels,
+                               cudaStream_t s);
+// stable counting sort by label: order[position] = id, offsets[p + 1]
+size_t kmed_sort_scratch_bytes(int64_t n, int p);
+cudaError_t launch_kmed_sort(const int32_t *labels, int64_t n, int p, void *scratch, int64_t *order,
+                             int64_t *offsets, cudaStream_t s);
+// medoid of every non-empty cluster (members order[offsets[m] .. offsets[m+1]))
+cudaError_t launch_kmed_update(int dp, const float *X, const int64_t *order, const int64_t *offsets, int p,
+                               int64_t *medoids, cudaStream_t s);
+
 // set the calling thread's knn_last_error() message (graph.cu)
 knn_status record_error(knn_status st, const char *msg);
 

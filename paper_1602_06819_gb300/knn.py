@@ -48,7 +48,7 @@ EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "
             "knn_graph_remove", "knn_graph_get_edges", "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
             "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
-            "knn_search_noalloc", "knn_last_error", "knn_version")
+            "knn_balanced_kmedoids", "knn_search_noalloc", "knn_last_error", "knn_version")
 
 EXACT_PATHS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
 
@@ -104,6 +104,7 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_destroy": (None, [P]),
         "knn_exact_graph": (I32, [P, I64, I32, I32, P, P, P]),
         "knn_exact_set_path": (I32, [I32]),
+        "knn_balanced_kmedoids": (I32, [P, I64, I32, I32, ctypes.c_double, I32, I32, U64, P, P, P, P, P]),
         "knn_graph_set_search": (I32, [P, ctypes.c_double, ctypes.c_double, I32]),
         "knn_exact_last_info": (I32, [ctypes.POINTER(KnnExactInfo)]),
         "knn_search_noalloc": (I32, [P, I64, I32, P, I32, P, I64, I32, ctypes.c_double,
@@ -245,6 +246,20 @@ def knn_exact_graph(X, k: int, out_ids, out_sims=None, stream=None) -> None:
     _check_dtype(out_sims, "float32", "out_sims")
     _check(lib.knn_exact_graph(_ptr(X), X.shape[0], X.shape[1], k, _ptr(out_ids), _ptr(out_sims),
                                _stream(stream)), "knn_exact_graph")
+
+
+def knn_balanced_kmedoids(X, p: int, imbalance: float, chunks: int, iters: int, seed: int,
+                          labels=None, medoids=None, order=None, offsets=None, stream=None) -> None:
+    """Balanced k-medoids (Algorithm 4) of X [n, dim] float32; outputs
+    labels [n] int32, medoids [p] int64, order [n] int64 (position -> point,
+    clusters contiguous), offsets [p + 1] int64, each optional."""
+    _check_dtype(X, "float32", "X")
+    _check_dtype(labels, "int32", "labels")
+    for name, arr in (("medoids", medoids), ("order", order), ("offsets", offsets)):
+        _check_dtype(arr, "int64", name)
+    _check(lib.knn_balanced_kmedoids(_ptr(X), X.shape[0], X.shape[1], p, float(imbalance), chunks,
+                                     iters, seed, _ptr(labels), _ptr(medoids), _ptr(order),
+                                     _ptr(offsets), _stream(stream)), "knn_balanced_kmedoids")
 
 
 def knn_exact_set_path(path: str) -> None:
