@@ -169,6 +169,29 @@ KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_
                                          int64_t *out_ids, float *out_sims, void *stream);
 
 /*
+ * Partitioned search (Sec. 6, Algorithm 3): every query is searched
+ * independently in each of `parts` partitions of the graph, then the k_out
+ * most similar of the parts * k_out candidates are kept.  Partition j is
+ * the node range part_offsets[j] .. part_offsets[j+1] - 1 (int64, host or
+ * device, [parts + 1], nondecreasing from 0 to n: for instance the clusters
+ * of knn_balanced_kmedoids after the points were stored in its order); its
+ * search is iGNNS (or the climb set by knn_graph_set_search) restricted to
+ * the subgraph: restart draws among its nodes, neighbour-list entries
+ * outside it not followed, budget max(1, floor(size / speedup)), so that the
+ * parts together compute about n / speedup similarities; its restart stream
+ * is 2^63 + query_id0 + i + j * 2^56 for query i.  Screening forms keep
+ * rescore_mult * k_out candidates per part and re-score the merged best
+ * rescore_mult * k_out in FP32.  knn_graph_last_counters then holds per
+ * query the sums over its parts.  1 <= parts <= min(KNN_MAX_PARTS,
+ * max_batch); other arguments and errors as knn_graph_query_batch.
+ */
+#define KNN_MAX_PARTS 1024
+KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                               uint64_t query_id0, const int64_t *part_offsets,
+                                               int32_t parts, int64_t *out_ids, float *out_sims,
+                                               void *stream);
+
+/*
  * Remove m nodes (not in the paper).  Removed nodes are never drawn, climbed
  * to, returned or offered again; lists that still hold them keep the entry.
  * KNN_ERR_NOT_FOUND if an id is outside 0 .. n-1.  ids: [m] int64.

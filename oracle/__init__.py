@@ -21,6 +21,7 @@ Every function cites the passage of the paper it follows:
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -266,6 +267,54 @@ def kmedoids(X, p: int, imbalance: float, chunks: int, iters: int, seed: int):
     _load().orc_kmedoids(_ptr(X), n, d, p, float(imbalance), chunks, iters, seed, _ptr(labels),
                          _ptr(med), ctypes.byref(g))
     return labels, med, g.value
+
+
+PART_STREAM_STEP = 1 << 56
+
+
+def partitioned_search(X, nbr_ids, q, k_out: int, part_offsets, speedup: float, expansion: float,
+                       seed: int, stream: int, removed=None, climb: str = "eager"):
+    """Distributed search (Sec. 6, Algorithm 3) with contiguous partitions:
+    partition j (nodes part_offsets[j] .. part_offsets[j+1]-1) is searched on
+    its own subgraph -- its rows, its lists with the entries that leave it
+    dropped -- with budget max(1, floor(size / speedup)) and restart stream
+    stream + j * 2^56; the k_out most similar of all candidates are kept.
+    Returns (ids, sims, summed SearchResult counters, margin)."""
+    X = _f32(X)
+    nbr = np.ascontiguousarray(nbr_ids, dtype=np.int64)
+    rem = None if removed is None else np.asarray(removed, dtype=np.uint8)
+    ids_all, sims_all = [], []
+    tot = dict(evals=0, restarts=0, discarded=0, moves=0, draws=0)
+    margin = math.inf
+    for j in range(len(part_offsets) - 1):
+        lo, hi = int(part_offsets[j]), int(part_offsets[j + 1])
+        if hi == lo:
+            continue
+        sub = nbr[lo:hi].copy()
+        inside = (sub >= lo) & (sub < hi)
+        sub = np.where(inside, sub - lo, -1)
+        r = search(X[lo:hi], sub, q, k_out, speedup, expansion, seed,
+                   (stream + j * PART_STREAM_STEP) % (1 << 64), n=hi - lo,
+                   removed=None if rem is None else rem[lo:hi], climb=climb)
+        for key in tot:
+            tot[key] += getattr(r, key)
+        margin = min(margin, r.margin)
+        ok = r.ids >= 0
+        ids_all.append(r.ids[ok] + lo)
+        sims_all.append(r.sims[ok])
+    ids = np.concatenate(ids_all) if ids_all else np.empty(0, np.int64)
+    sims = np.concatenate(sims_all) if sims_all else np.empty(0)
+    order = np.lexsort((ids, -sims))          # similarity descending, then id
+    ids, sims = ids[order], sims[order]
+    if len(sims) > k_out:                     # the boundary of the kept set
+        a, b = sims[k_out - 1], sims[k_out]
+        if a != b:
+            margin = min(margin, abs(a - b) / max(abs(a), abs(b)))
+    out_ids = np.full(k_out, -1, np.int64)
+    out_sims = np.full(k_out, -np.inf)
+    kk = min(k_out, len(ids))
+    out_ids[:kk], out_sims[:kk] = ids[:kk], sims[:kk]
+    return out_ids, out_sims, tot, margin
 
 
 def rescore(X, q, cand_ids, k_out: int):

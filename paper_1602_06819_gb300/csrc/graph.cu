@@ -60,6 +60,11 @@ struct knn_graph {
     uint64_t *keys_search = nullptr;
     uint64_t *keys_final = nullptr;
     long long *counters = nullptr;
+    uint64_t *keys_merge = nullptr;      // partitioned queries: merged candidates [M][KT]
+    long long *counters_q = nullptr;     // partitioned queries: per-query counters [M][NCTR]
+    int64_t *part_off = nullptr;         // [KNN_MAX_PARTS + 1]
+    int64_t *part_live = nullptr;        // [KNN_MAX_PARTS]
+    const long long *last_counters_src = nullptr;
     uint64_t *offer_key = nullptr;
     int32_t *offer_next = nullptr;
     int32_t *touched = nullptr;
@@ -276,7 +281,10 @@ static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int 
     a.discard = (e > 0.0 && std::isfinite(e)) ? 1 : 0;
     a.expansion = a.discard ? (float)e : 1.0f;
     a.climb = g->climb;
+    a.vis_n = (uint32_t)g->n;
+    a.speedup = g->p.speedup;
     CU(launch_search(g->p.storage, g->dp, a, s));
+    g->last_counters_src = g->counters;
     ++g->launches;
     g->phase_ran[KNN_PHASE_SEARCH] = true;
     phase_mark(g, KNN_PHASE_RESCORE, s);
@@ -383,7 +391,8 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
     size_t need = (size_t)C * DP * 4 + (size_t)C * K * 8 + (size_t)g->vwords * 4 + (size_t)C * 4 +
                   (size_t)M * g->vwords * 4 + (size_t)M * DP * 4 + (size_t)M * p.dim * 4 +
                   (size_t)M * g->KT * 8 + (size_t)M * K * 8 + (size_t)M * NCTR * 8 +
-                  (size_t)g->offer_cap * 16 + (size_t)M * K * 12 + (size_t)M * levels * 4;
+                  (size_t)g->offer_cap * 16 + (size_t)M * K * 12 + (size_t)M * levels * 4 +
+                  (size_t)M * g->KT * 8 + (size_t)M * NCTR * 8 + (size_t)(2 * KNN_MAX_PARTS + 1) * 8;
     if (p.storage == KNN_STORAGE_BF16) need += (size_t)C * DP * 2;
     if (p.storage == KNN_STORAGE_FP8_E4M3) need += (size_t)C * DP + (size_t)C * 4;
     size_t free_b = 0, total_b = 0;
@@ -413,6 +422,10 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
     ALLOC(keys_search, M * g->KT)
     ALLOC(keys_final, M * K)
     ALLOC(counters, M * NCTR)
+    ALLOC(keys_merge, M * g->KT)
+    ALLOC(counters_q, M * NCTR)
+    ALLOC(part_off, KNN_MAX_PARTS + 1)
+    ALLOC(part_live, KNN_MAX_PARTS)
     ALLOC(offer_key, g->offer_cap)
     ALLOC(offer_next, g->offer_cap)
     ALLOC(touched, g->offer_cap)
@@ -649,6 +662,118 @@ KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_
     return KNN_OK;
 }
 
+KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                               uint64_t query_id0, const int64_t *part_offsets, int32_t parts,
+                                               int64_t *out_ids, float *out_sims, void *stream) {
+    if (!g || !vecs || !out_ids || !part_offsets) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (m < 1 || m > g->p.max_batch)
+        return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
+    if (k_out < 1 || k_out > g->p.k) return fail(KNN_ERR_INVALID_ARG, "k_out outside 1..k");
+    if (parts < 1 || parts > KNN_MAX_PARTS || parts > g->p.max_batch)
+        return fail(KNN_ERR_UNSUPPORTED, "parts %d outside 1..min(%d, max_batch)", parts, KNN_MAX_PARTS);
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    // the partitions: contiguous id ranges covering the graph
+    std::vector<int64_t> off((size_t)parts + 1);
+    if (is_device_ptr(part_offsets)) {
+        CU(cudaMemcpyAsync(off.data(), part_offsets, off.size() * 8, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(off.data(), part_offsets, off.size() * 8);
+    }
+    if (off[0] != 0 || off[(size_t)parts] != g->n)
+        return fail(KNN_ERR_INVALID_ARG, "partition offsets must run from 0 to n = %lld", (long long)g->n);
+    std::vector<int64_t> live((size_t)parts);
+    int64_t largest = 0;
+    for (int q = 0; q < parts; ++q) {
+        if (off[(size_t)q + 1] < off[(size_t)q]) return fail(KNN_ERR_INVALID_ARG, "partition offsets decrease");
+        int64_t rem = 0;
+        for (int64_t v = off[(size_t)q]; v < off[(size_t)q + 1]; ++v)
+            rem += (g->removed_host[(size_t)(v >> 5)] >> (v & 31)) & 1u;
+        live[(size_t)q] = off[(size_t)q + 1] - off[(size_t)q] - rem;
+        largest = std::max(largest, off[(size_t)q + 1] - off[(size_t)q]);
+    }
+    CU(cudaMemcpyAsync(g->part_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(g->part_live, live.data(), live.size() * 8, cudaMemcpyHostToDevice, s));
+    phase_begin_call(g);
+    phase_mark(g, KNN_PHASE_STORE, s);
+    TRY(append_rows(g, vecs, m, 0, g->qbuf, false, s));
+    g->phase_ran[KNN_PHASE_STORE] = true;
+    phase_mark(g, KNN_PHASE_SEARCH, s);
+    const bool screening = g->p.storage != KNN_STORAGE_FP32;
+    const int KT = screening ? g->p.rescore_mult * k_out : k_out;
+    // searches of one launch: parts per query, at most max_batch of them
+    const int64_t step = std::max<int64_t>(1, g->p.max_batch / parts);
+    const int64_t words = (largest + 31) / 32;
+    bool synced = false;
+    for (int64_t q0 = 0; q0 < m; q0 += step) {
+        const int64_t mq = std::min(step, m - q0);
+        if (!search_visited_on_chip((uint32_t)largest))
+            CU(cudaMemsetAsync(g->visited, 0, (size_t)mq * parts * words * sizeof(uint32_t), s));
+        SearchArgs a{};
+        a.rows = searched_rows(g);
+        a.row_scale = g->scale;
+        a.nbr = g->nbr_ids;
+        a.removed = g->removed;
+        a.queries = g->qbuf + (size_t)q0 * g->dp;
+        a.q_stride = g->dp;
+        a.visited = g->visited;
+        a.vwords = words;
+        a.out_keys = g->keys_search;
+        a.counters = g->counters;
+        a.totals = g->totals;
+        a.m = (int32_t)mq;
+        a.k = g->p.k;
+        a.KT = KT;
+        a.n = (uint32_t)g->n;
+        a.n_live = g->n - g->n_removed;
+        a.budget = budget_of(g->n, g->p.speedup);
+        a.max_draws = 64ull * (uint64_t)g->n;
+        a.seed = g->p.seed;
+        a.stream_base = (1ull << 63) + query_id0 + (uint64_t)q0;
+        const double e = g->p.expansion;
+        a.discard = (e > 0.0 && std::isfinite(e)) ? 1 : 0;
+        a.expansion = a.discard ? (float)e : 1.0f;
+        a.climb = g->climb;
+        a.parts = parts;
+        a.part_off = g->part_off;
+        a.part_live = g->part_live;
+        a.speedup = g->p.speedup;
+        a.vis_n = (uint32_t)largest;
+        CU(launch_search(g->p.storage, g->dp, a, s));
+        // the k_out (or KT) best of each query's parts * KT candidates
+        CU(launch_merge_parts(g->keys_search, (int32_t)mq, parts, KT, g->keys_merge, g->counters,
+                              g->counters_q + (size_t)q0 * NCTR, s));
+        g->launches += 2;
+        const uint64_t *keys = g->keys_merge;
+        if (screening) {
+            RescoreArgs r{};
+            r.rows = g->X;
+            r.queries = a.queries;
+            r.q_stride = g->dp;
+            r.cand_keys = g->keys_merge;
+            r.out_keys = g->keys_final;
+            r.totals = g->totals;
+            r.m = (int32_t)mq;
+            r.KT = KT;
+            r.k_out = k_out;
+            CU(launch_rescore(g->dp, r, s));
+            ++g->launches;
+            keys = g->keys_final;
+        }
+        TRY(emit_keys(g, keys, mq, k_out, k_out, out_ids + q0 * k_out, out_sims ? out_sims + q0 * k_out : nullptr, s,
+                      &synced));
+    }
+    g->phase_ran[KNN_PHASE_SEARCH] = true;
+    phase_mark(g, KNN_PHASE_RESCORE, s);
+    for (int ph = KNN_PHASE_RESCORE + 1; ph <= KNN_NUM_PHASES; ++ph) phase_mark(g, ph, s);
+    g->last_counters_src = g->counters_q;
+    g->queries += m;
+    g->last_m = m;
+    return KNN_OK;
+}
+
 KNN_API knn_status knn_graph_remove(knn_graph *g, const int64_t *ids, int64_t m, void *stream) {
     if (!g || (!ids && m > 0)) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 0) return fail(KNN_ERR_INVALID_ARG, "negative m");
@@ -717,7 +842,7 @@ KNN_API knn_status knn_graph_last_counters(knn_graph *g, int64_t *out, int64_t m
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool dev = is_device_ptr(out);
-    CU(cudaMemcpyAsync(out, g->counters, (size_t)m * NCTR * 8,
+    CU(cudaMemcpyAsync(out, g->last_counters_src ? g->last_counters_src : g->counters, (size_t)m * NCTR * 8,
                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (!dev) CU(cudaStreamSynchronize(s));
     return KNN_OK;

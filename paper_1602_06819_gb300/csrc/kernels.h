@@ -62,7 +62,18 @@ struct SearchArgs {
     float expansion;
     int32_t discard;             // expansion test enabled
     int32_t climb;               // KNN_CLIMB_EAGER (iGNNS) or KNN_CLIMB_BEST (GNNS)
+    // partitioned search (Algorithm 3): parts > 1 runs m * parts searches,
+    // search s = query s / parts over the nodes part_off[p] .. part_off[p+1]-1
+    // (p = s % parts) with budget max(1, floor(size / speedup)) and restart
+    // stream stream_base + query + p * PART_STREAM_STEP; keys and counters
+    // are then per search.  parts == 1: every node, budget and n_live as set.
+    int32_t parts = 1;
+    const int64_t *part_off = nullptr;   // [parts + 1] device
+    const int64_t *part_live = nullptr;  // [parts] live nodes of each partition
+    double speedup = 1.0;
+    uint32_t vis_n = 0;                  // bits of one visited set (n, or the largest partition)
 };
+constexpr uint64_t PART_STREAM_STEP = 1ull << 56;
 
 struct RescoreArgs {
     const float *rows;           // FP32 padded rows
@@ -167,6 +178,12 @@ cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned 
 // snapshot restore: copy int64 lists (checking every id) and recompute their d2
 cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,
                                  int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s);
+
+// partitioned search: per query, the k_keep best of its parts * k_keep
+// candidate keys ([m * parts][k_keep] -> [m][k_keep]) and the sums of its
+// searches' counters ([m * parts][NCTR] -> [m][NCTR]) (misc.cu)
+cudaError_t launch_merge_parts(const uint64_t *keys, int32_t m, int32_t parts, int32_t k_keep, uint64_t *out,
+                               const long long *ctr_in, long long *ctr_out, cudaStream_t s);
 
 // balanced k-medoids (kmedoids.cu); X are padded FP32 rows [n][dp]
 constexpr int KMED_MAX_P = 1024;

@@ -106,6 +106,53 @@ cudaError_t launch_lists_to_output(const int32_t *ids, const float *d2, int64_t 
     return cudaGetLastError();
 }
 
+// One warp per query (Algorithm 3, "keep k most similar nodes"): the keys of
+// its searches are distinct nodes, so the best k_keep of their union is the
+// merged list; counters add up.
+template <int T>
+__global__ void merge_parts_kernel(const uint64_t *keys, int32_t m, int32_t parts, int32_t k_keep, uint64_t *out,
+                                   const long long *ctr_in, long long *ctr_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (qi >= m) return;  // warp-uniform
+    WarpTop<T> top;
+    top.init(k_keep);
+    for (int p = 0; p < parts; ++p) {
+        const uint64_t *src = keys + ((size_t)qi * parts + p) * k_keep;
+        for (int i0 = 0; i0 < k_keep; i0 += 32) {
+            const uint64_t key = i0 + lane < k_keep ? src[i0 + lane] : KEY_EMPTY;
+            unsigned om = __ballot_sync(FULL, key < top.worst);
+            while (om) {
+                const int l = __ffs(om) - 1;
+                top.offer(shfl_u64(key, l));
+                om &= ~(1u << l);
+                om &= __ballot_sync(FULL, key < top.worst);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int idx = t * 32 + lane;
+        if (idx < k_keep) out[(size_t)qi * k_keep + idx] = top.e[t];
+    }
+    if (lane < NCTR) {
+        long long sum = 0;
+        for (int p = 0; p < parts; ++p) sum += ctr_in[((size_t)qi * parts + p) * NCTR + lane];
+        ctr_out[(size_t)qi * NCTR + lane] = sum;
+    }
+}
+
+cudaError_t launch_merge_parts(const uint64_t *keys, int32_t m, int32_t parts, int32_t k_keep, uint64_t *out,
+                               const long long *ctr_in, long long *ctr_out, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((m * 32 + 127) / 128);
+    if (k_keep <= 32)
+        merge_parts_kernel<1><<<blocks, 128, 0, s>>>(keys, m, parts, k_keep, out, ctr_in, ctr_out);
+    else
+        merge_parts_kernel<4><<<blocks, 128, 0, s>>>(keys, m, parts, k_keep, out, ctr_in, ctr_out);
+    return cudaGetLastError();
+}
+
 __global__ void fill_ids_kernel(int64_t *out, int64_t first, int64_t m) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m) out[t] = first + t;

@@ -152,6 +152,8 @@ extern "C" KNN_API knn_status knn_search_noalloc(const float *rows, int64_t n, i
     a.stream_base = (1ull << 63) + query_id0;
     a.discard = (expansion > 0.0 && std::isfinite(expansion)) ? 1 : 0;
     a.expansion = a.discard ? (float)expansion : 1.0f;
+    a.vis_n = (uint32_t)n;
+    a.speedup = speedup;
     e = launch_search(KNN_STORAGE_FP32, dim, a, s);
     if (e == cudaSuccess) e = launch_keys_to_output(keys, m, k_out, k_out, out_ids, out_sims, s);
     if (e != cudaSuccess) return reject(KNN_ERR_CUDA, "launch failed: %s", cudaGetErrorString(e));

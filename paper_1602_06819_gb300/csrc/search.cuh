@@ -49,16 +49,22 @@ __device__ __forceinline__ bool test_bit_ro(const uint32_t *bits, uint32_t i) {
     return (ld_nc_u32(bits + (i >> 5)) >> (i & 31)) & 1u;
 }
 
-// A query's visited set: a bitset in shared memory or in global memory.
+// A search's visited set over the nodes base .. base + size - 1: a bitset in
+// shared memory or in global memory.
 template <bool SMEM>
 struct Visited {
     uint32_t *bits;
-    __device__ __forceinline__ bool test(uint32_t i) const {
+    uint32_t base;
+    __device__ __forceinline__ bool test(uint32_t id) const {
+        const uint32_t i = id - base;
         if constexpr (SMEM) return (bits[i >> 5] >> (i & 31)) & 1u;
         // global bits are set with atomics at L2; read them from L2 too
         return (ld_cg_u32(bits + (i >> 5)) >> (i & 31)) & 1u;
     }
-    __device__ __forceinline__ void mark(uint32_t i) const { atomicOr(bits + (i >> 5), 1u << (i & 31)); }
+    __device__ __forceinline__ void mark(uint32_t id) const {
+        const uint32_t i = id - base;
+        atomicOr(bits + (i >> 5), 1u << (i & 31));
+    }
 };
 
 // Shared memory a block may use for visited sets (two blocks per SM); the
@@ -108,22 +114,36 @@ ignns_search_kernel(const SearchArgs a) {
     const RowSource src{a.rows, a.row_scale};
     const int nwarps = gridDim.x * SEARCH_WARPS;
     const float INF = __int_as_float(0x7f800000);
-    // each evaluation visits a new node, so evals also counts visited nodes
-    const int limit = (int)(a.budget < a.n_live ? a.budget : a.n_live);
+    const int nsearch = a.m * a.parts;
 
-    for (int qi = blockIdx.x * SEARCH_WARPS + wib; qi < a.m; qi += nwarps) {
+    // search sw: query sw / parts over partition sw % parts, the nodes
+    // lo .. lo + np - 1 (one partition: every node)
+    for (int sw = blockIdx.x * SEARCH_WARPS + wib; sw < nsearch; sw += nwarps) {
+        const int qi = sw / a.parts, part = sw % a.parts;
+        const uint32_t lo = a.parts > 1 ? (uint32_t)a.part_off[part] : 0u;
+        const uint32_t np = a.parts > 1 ? (uint32_t)(a.part_off[part + 1] - (int64_t)lo) : a.n;
+        const int64_t live = a.parts > 1 ? a.part_live[part] : a.n_live;
+        int64_t budget = a.budget;
+        if (a.parts > 1) {
+            const double b = floor((double)np / a.speedup);  // max(1, floor(n / speedup))
+            budget = b < 1.0 ? 1 : (int64_t)b;
+        }
+        const uint64_t max_draws = a.parts > 1 ? 64ull * np : a.max_draws;
+        // each evaluation visits a new node, so evals also counts visited nodes
+        const int limit = (int)(budget < live ? budget : live);
         float qv[C::QF];
         load_query<STORAGE, DP>(a.queries + (size_t)qi * a.q_stride, qv);
         Visited<SMEM_VIS> vis;
+        vis.base = lo;
         if constexpr (SMEM_VIS) {
-            const uint32_t words = (a.n + 31) / 32;
-            vis.bits = s_visited + (size_t)wib * words;
-            for (uint32_t w = lane; w < words; w += 32) vis.bits[w] = 0u;
+            vis.bits = s_visited + (size_t)wib * ((a.vis_n + 31) / 32);
+            for (uint32_t w = lane; w < (np + 31) / 32; w += 32) vis.bits[w] = 0u;
             __syncwarp();
         } else {
-            vis.bits = a.visited + (size_t)qi * a.vwords;
+            vis.bits = a.visited + (size_t)sw * a.vwords;
         }
-        const uint64_t rkey = restart_key(a.seed, a.stream_base + (uint64_t)qi);
+        const uint64_t rkey =
+            restart_key(a.seed, a.stream_base + (uint64_t)qi + (uint64_t)part * PART_STREAM_STEP);
 
         WarpTop<T> top;
         top.init(a.KT);
@@ -139,10 +159,10 @@ ignns_search_kernel(const SearchArgs a) {
         auto draw = [&](int want, uint32_t &id, uint64_t &dj) -> int {
             int nc = 0;
             __syncwarp();  // marks made so far are visible to the bit reads
-            while (nc < want && j < a.max_draws) {
+            while (nc < want && j < max_draws) {
                 const uint64_t jj = j + (uint64_t)lane;
-                const bool valid = jj < a.max_draws;
-                const uint32_t r = valid ? restart_node(rkey, jj, a.n) : 0u;
+                const bool valid = jj < max_draws;
+                const uint32_t r = valid ? lo + restart_node(rkey, jj, np) : lo;
                 const bool good = valid && !test_bit_ro(a.removed, r) && !vis.test(r);
                 const unsigned bal = __ballot_sync(FULL, good);
                 const int avail = __popc(bal);
@@ -159,7 +179,7 @@ ignns_search_kernel(const SearchArgs a) {
                 } else {
                     j += 32u;
                 }
-                if (j > a.max_draws) j = a.max_draws;
+                if (j > max_draws) j = max_draws;
                 nc += take;
             }
             __syncwarp();
@@ -233,7 +253,8 @@ ignns_search_kernel(const SearchArgs a) {
                 while (true) {
                     const int32_t nb = lane < a.k ? (int32_t)ld_nc_u32(a.nbr + (size_t)cur * a.k + lane) : -1;
                     ++adj;
-                    const bool valid = nb >= 0 && !test_bit_ro(a.removed, (uint32_t)nb);
+                    // a partition follows only its own nodes (Algorithm 3)
+                    const bool valid = nb >= 0 && (uint32_t)nb - lo < np && !test_bit_ro(a.removed, (uint32_t)nb);
                     __syncwarp();
                     const bool seen = valid && vis.test((uint32_t)nb);
                     const float nd2 = gather_d2<STORAGE, DP>(src, valid ? (uint32_t)nb : 0u, a.k, qv);
@@ -303,10 +324,10 @@ ignns_search_kernel(const SearchArgs a) {
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const int idx = t * 32 + lane;
-            if (idx < a.KT) a.out_keys[(size_t)qi * a.KT + idx] = top.e[t];
+            if (idx < a.KT) a.out_keys[(size_t)sw * a.KT + idx] = top.e[t];
         }
         if (lane == 0) {
-            long long *ctr = a.counters + (size_t)qi * NCTR;
+            long long *ctr = a.counters + (size_t)sw * NCTR;
             ctr[CTR_SEARCH_EVALS] = evals;
             ctr[CTR_UPDATE_EVALS] = 0;
             ctr[CTR_RESTARTS] = restarts;
@@ -328,8 +349,8 @@ ignns_search_kernel(const SearchArgs a) {
 
 template <int ST, int DPV, int T>
 static cudaError_t launch_search_t(const SearchArgs &a, cudaStream_t s) {
-    const int grid = (a.m + SEARCH_WARPS - 1) / SEARCH_WARPS;
-    const size_t smem = search_smem_bytes(a.n);
+    const int grid = (a.m * a.parts + SEARCH_WARPS - 1) / SEARCH_WARPS;
+    const size_t smem = search_smem_bytes(a.vis_n);
     if (smem <= SEARCH_SMEM_VIS_MAX) {
         cudaError_t e = cudaFuncSetAttribute(ignns_search_kernel<ST, DPV, T, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -45,7 +45,8 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
 
 # Every symbol include/knn_graph.h declares.
 EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
-            "knn_graph_remove", "knn_graph_get_edges", "knn_graph_last_counters",
+            "knn_graph_query_partitioned", "knn_graph_remove", "knn_graph_get_edges",
+            "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
             "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
             "knn_balanced_kmedoids", "knn_search_noalloc", "knn_last_error", "knn_version")
@@ -95,6 +96,7 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_restore": (I32, [ctypes.POINTER(KnnParams), P, I64, P, P, ctypes.POINTER(P)]),
         "knn_graph_insert_batch": (I32, [P, P, I64, P, P, P]),
         "knn_graph_query_batch": (I32, [P, P, I64, I32, U64, P, P, P]),
+        "knn_graph_query_partitioned": (I32, [P, P, I64, I32, U64, P, I32, P, P, P]),
         "knn_graph_remove": (I32, [P, P, I64, P]),
         "knn_graph_get_edges": (I32, [P, P, P, I64, ctypes.POINTER(I64), P]),
         "knn_graph_last_counters": (I32, [P, P, I64, P]),
@@ -191,6 +193,20 @@ def knn_graph_query_batch(g, vecs, k_out: int, query_id0: int, out_ids, out_sims
     _check_dtype(out_sims, "float32", "out_sims")
     _check(lib.knn_graph_query_batch(g, _ptr(vecs), vecs.shape[0], k_out, query_id0, _ptr(out_ids),
                                      _ptr(out_sims), _stream(stream)), "knn_graph_query_batch")
+
+
+def knn_graph_query_partitioned(g, vecs, k_out: int, query_id0: int, part_offsets, out_ids,
+                                out_sims=None, stream=None) -> None:
+    """Algorithm 3: search each partition (node ranges part_offsets[j] ..
+    part_offsets[j+1]-1, int64 [parts + 1]) and keep the k_out best."""
+    _check_dtype(vecs, "float32", "vecs")
+    _check_dtype(part_offsets, "int64", "part_offsets")
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_sims, "float32", "out_sims")
+    _check(lib.knn_graph_query_partitioned(g, _ptr(vecs), vecs.shape[0], k_out, query_id0,
+                                           _ptr(part_offsets), part_offsets.shape[0] - 1,
+                                           _ptr(out_ids), _ptr(out_sims), _stream(stream)),
+           "knn_graph_query_partitioned")
 
 
 def knn_graph_remove(g, ids, stream=None) -> None:
@@ -333,6 +349,11 @@ class Graph:
 
     def query(self, vecs, k_out, query_id0, out_ids, out_sims=None, stream=None):
         knn_graph_query_batch(self.handle, vecs, k_out, query_id0, out_ids, out_sims, stream)
+
+    def query_partitioned(self, vecs, k_out, query_id0, part_offsets, out_ids, out_sims=None,
+                          stream=None):
+        knn_graph_query_partitioned(self.handle, vecs, k_out, query_id0, part_offsets, out_ids,
+                                    out_sims, stream)
 
     def remove(self, ids, stream=None):
         knn_graph_remove(self.handle, ids, stream)

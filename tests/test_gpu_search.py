@@ -251,3 +251,106 @@ def test_query_results_do_not_depend_on_the_batch(knn):
             assert np.array_equal(part, all_ids[s:s + 9])
     finally:
         g.close()
+
+
+# ---------------------------------------------------------------------------
+# partitioned search (Sec. 6, Algorithm 3)
+# ---------------------------------------------------------------------------
+
+def compare_partitioned(knn, X0, Q, k, k_out, speedup, e, seed, offs, storage=0, removed=None,
+                        climb="eager", max_batch=256, max_ambiguous=0.4):
+    import torch
+    n, d = X0.shape
+    o_ids, _, _ = oracle.exact_knn(X0, k)
+    g = make_graph(knn, X0, k, speedup, e, seed, storage, 4, max_batch=max_batch, nbr_ids=o_ids)
+    m = Q.shape[0]
+    try:
+        if climb != "eager":
+            g.set_search(speedup, e, climb)
+        rem = None
+        if removed is not None:
+            g.remove(torch.as_tensor(removed, dtype=torch.int64))
+            rem = np.zeros(n, np.uint8)
+            rem[removed] = 1
+        qid0 = 500
+        ids = torch.empty((m, k_out), dtype=torch.int64, device="cuda")
+        sims = torch.empty((m, k_out), dtype=torch.float32, device="cuda")
+        g.query_partitioned(cuda_tensor(Q), k_out, qid0, torch.as_tensor(offs, dtype=torch.int64), ids, sims)
+        ctr = np.empty((m, 8), np.int64)
+        g.counters(ctr)
+        torch.cuda.synchronize()
+        ids, sims = ids.cpu().numpy(), sims.cpu().numpy()
+    finally:
+        g.close()
+    Xs = X0
+    if storage == 1:
+        _, Xs = oracle.quantize_bf16(X0)
+    elif storage == 2:
+        _, _, Xs = oracle.quantize_e4m3(X0)
+    tol = gather_tol(d, storage)
+    ambiguous = 0
+    for i, q in enumerate(Q):
+        kt = k_out if storage == 0 else 4 * k_out
+        e_ids, e_sims, tot, margin = oracle.partitioned_search(Xs, o_ids, q, kt, offs, speedup, e, seed,
+                                                               (1 << 63) + qid0 + i, removed=rem,
+                                                               climb=climb)
+        if storage != 0:
+            e_ids, e_sims, m2 = oracle.rescore(X0, q, e_ids, k_out)
+            margin = min(margin, m2)
+        if margin < tol:
+            ambiguous += 1
+            continue
+        assert list(ids[i]) == list(e_ids), f"query {i}"
+        valid = e_ids >= 0
+        assert rel_err(sims[i][valid], e_sims[valid]).max() <= 1e-5
+        got = tuple(ctr[i][[0, 2, 3, 4, 6]])
+        want = (tot["evals"], tot["restarts"], tot["discarded"], tot["moves"], tot["draws"])
+        assert got == want, f"query {i}: counters {got} != {want}"
+    assert ambiguous <= max_ambiguous * len(Q), f"{ambiguous} of {len(Q)} ambiguous"
+
+
+@pytest.mark.parametrize("d,n,offs,speedup,e", [
+    (16, 1000, [0, 250, 500, 750, 1000], 4.0, 5.0),
+    (16, 1000, [0, 37, 400, 401, 1000], 2.0, math.inf),   # uneven parts, one of a single node
+    (128, 3000, [0, 300, 700, 1100, 1500, 1800, 2300, 2600, 3000], 8.0, 5.0),
+])
+def test_partitioned_queries(knn, d, n, offs, speedup, e):
+    mix = Mixture(d=d, components=10, half_width=10.0 if d == 16 else 20.0, sigma=1.0, seed=14)
+    X0, Q = mix.sample(n, 1), mix.sample(64, 3)
+    compare_partitioned(knn, X0, Q, 10, 10, speedup, e, seed=4, offs=offs, max_ambiguous=0.6)
+
+
+def test_partitioned_queries_kmedoids_order_screened_removed_gnns(knn):
+    """Partitions from the balanced k-medoids ordering of the points, BF16
+    screening with FP32 re-score, removed nodes, the GNNS climb, and more
+    queries than one launch holds (max_batch 32 with 8 parts: 4 queries a
+    launch)."""
+    mix = Mixture(d=32, components=8, half_width=10.0, sigma=1.0, seed=15)
+    X = mix.sample(2000, 1)
+    labels, _, _ = oracle.kmedoids(X, 8, 1.1, 1, 1, seed=3)
+    order = np.lexsort((np.arange(2000), labels))
+    X0 = np.ascontiguousarray(X[order])
+    offs = np.concatenate([[0], np.cumsum(np.bincount(labels, minlength=8))]).tolist()
+    Q = mix.sample(20, 3)
+    removed = np.random.default_rng(4).choice(2000, 50, replace=False)
+    compare_partitioned(knn, X0, Q, 8, 8, 2.0, math.inf, seed=2, offs=offs, storage=1, removed=removed,
+                        climb="best", max_batch=32, max_ambiguous=0.6)
+
+
+def test_partitioned_one_part_equals_query_batch(knn):
+    import torch
+    mix = Mixture(d=16, components=6, half_width=10.0, sigma=1.0, seed=16)
+    X0, Q = mix.sample(800, 1), mix.sample(32, 2)
+    g = make_graph(knn, X0, 8, 4.0, 5.0, seed=3)
+    try:
+        a, _, ca = run_queries(g, Q, 8, 77)
+        b = torch.empty((32, 8), dtype=torch.int64, device="cuda")
+        g.query_partitioned(cuda_tensor(Q), 8, 77, torch.tensor([0, 800], dtype=torch.int64), b)
+        cb = np.empty((32, 8), np.int64)
+        g.counters(cb)
+        torch.cuda.synchronize()
+        with pytest.raises(knn.KnnError):
+            g.query_partitioned(cuda_tensor(Q), 8, 77, torch.tensor([0, 500], dtype=torch.int64), b)
+    finally:
+        g.close()
+    assert np.array_equal(a, b.cpu().numpy()) and np.array_equal(ca, cb)

@@ -504,3 +504,63 @@ def test_kmedoids_iterations(orc):
     again, _ = orc.kmedoids_assign(X, med, 1.2, 3)
     assert np.array_equal(labels, again)
     assert np.bincount(labels, minlength=6).min() > 0
+
+
+# ---------------------------------------------------------------------------
+# partitioned search (Sec. 6, Algorithm 3)
+# ---------------------------------------------------------------------------
+
+def test_partitioned_search_one_part_is_the_search(orc):
+    mix = Mixture(d=8, components=5, half_width=5.0, sigma=1.0, seed=3)
+    X = mix.sample(400, 1)
+    nbr, _, _ = orc.exact_knn(X, 6)
+    for i, q in enumerate(mix.sample(5, 2)):
+        ids, sims, tot, _ = orc.partitioned_search(X, nbr, q, 5, [0, 400], 4.0, 5.0, seed=2, stream=i)
+        r = orc.search(X, nbr, q, 5, 4.0, 5.0, seed=2, stream=i)
+        assert list(ids) == list(r.ids) and tot["evals"] == r.evals and tot["moves"] == r.moves
+
+
+def test_partitioned_search_exhaustive_and_budget(orc):
+    """speedup 1 without the expansion test searches every partition
+    exhaustively, so the merged list is the exact k nearest whatever the
+    partitions; otherwise the parts spend max(1, floor(size / speedup))
+    each."""
+    mix = Mixture(d=8, components=5, half_width=5.0, sigma=1.0, seed=4)
+    X = mix.sample(500, 1)
+    nbr, _, _ = orc.exact_knn(X, 6)
+    offs = [0, 90, 260, 261, 500]
+    Xd = X.astype(np.float64)
+    for i, q in enumerate(mix.sample(6, 2)):
+        ids, sims, tot, _ = orc.partitioned_search(X, nbr, q, 8, offs, 1.0, math.inf, seed=1, stream=i)
+        s = 1.0 / (1.0 + np.linalg.norm(Xd - q.astype(np.float64), axis=1))
+        assert list(ids) == list(np.lexsort((np.arange(500), -s))[:8])
+        assert tot["evals"] == 500
+        _, _, tot, _ = orc.partitioned_search(X, nbr, q, 8, offs, 7.0, 5.0, seed=1, stream=i)
+        assert tot["evals"] == sum(max(1, math.floor((b - a) / 7.0)) for a, b in zip(offs, offs[1:]))
+
+
+def test_partitioned_search_draw_streams(orc):
+    """With a budget of one similarity per part, part j evaluates exactly its
+    first restart draw of stream s + j 2^56 among its own nodes."""
+    X = Mixture(d=4, components=3, half_width=5.0, sigma=1.0, seed=5).sample(300, 1)
+    nbr, _, _ = orc.exact_knn(X, 4)
+    offs = [0, 100, 220, 300]
+    q = X[7] + 0.1
+    s0 = (1 << 63) + 42
+    ids, _, tot, _ = orc.partitioned_search(X, nbr, q, 3, offs, 1000.0, 5.0, seed=9, stream=s0)
+    want = [a + orc.draw(orc.search_key(9, (s0 + j * (1 << 56)) % (1 << 64)), 0, b - a)
+            for j, (a, b) in enumerate(zip(offs, offs[1:]))]
+    assert sorted(ids.tolist()) == sorted(want) and tot["evals"] == 3
+
+
+def test_partitioned_search_does_not_leave_its_part(orc):
+    """Lists of part 0 that point only into part 1 give part 0 nothing to
+    climb to: its search is restarts only."""
+    X = Mixture(d=4, components=2, half_width=5.0, sigma=1.0, seed=6).sample(200, 1)
+    nbr = np.empty((200, 4), np.int64)
+    nbr[:100] = 100 + (np.arange(100)[:, None] * 7 + np.arange(4)) % 100   # part 0 -> part 1
+    nbr[100:] = (np.arange(100)[:, None] * 3 + np.arange(4)) % 100 + 100   # part 1 -> itself
+    ids, _, tot, _ = orc.partitioned_search(X, nbr, X[3], 5, [0, 100], 4.0, math.inf, seed=3,
+                                            stream=11)
+    assert tot["moves"] == 0 and tot["restarts"] == tot["evals"] == 25
+    assert np.all(ids < 100)
