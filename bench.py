@@ -58,7 +58,10 @@ def parse_args():
     ap.add_argument("--storage", default=None, choices=("fp32", "bf16", "fp8"),
                     help="searched copy of the rows (default: fp32; bf16 for precision)")
     ap.add_argument("--rescore-mult", type=int, default=4)
-    ap.add_argument("--experiment", default=None, choices=("search", "depth"),
+    ap.add_argument("--order", default="none", choices=("none", "kmedoids"),
+                    help="store the initial points in the order of their balanced k-medoids "
+                         "clusters (Algorithm 4; n/1000 clusters) before building the graph")
+    ap.add_argument("--experiment", default=None, choices=("search", "depth", "partitions"),
                     help="instead of the benchmark line: the search sweeps (expansion e; "
                          "iGNNS against GNNS at equal evaluations) or the DEPTH sweep, "
                          "one JSON line per point")
@@ -317,7 +320,14 @@ def workload_config(args, W):
            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
     if args.storage != "fp32":
         cfg["rescore"] = f"FP32 re-score of the best {args.rescore_mult}k screening candidates"
+    if args.order != "none":
+        cfg["order"] = (f"initial points stored by balanced k-medoids cluster "
+                        f"({kmedoids_clusters(W.n_init)} clusters, imbalance 1.1, 8 chunks, 1 update)")
     return cfg
+
+
+def kmedoids_clusters(n):
+    return max(1, min(1024, n // 1000))
 
 
 # ---------------------------------------------------------------------------
@@ -425,6 +435,61 @@ def run_depth_experiment(knn, torch, np):
                       update_evals_per_insert=update, inserts_per_s=na / secs)
 
 
+def run_partition_experiment(knn, torch, np):
+    """Partitioned search (Algorithm 3) on the default workload's 100,000
+    initial points stored in the order of P balanced k-medoids clusters:
+    recall@10 against exhaustive search, similarities per query, the time of
+    a 1,024-query batch and the latency of single queries, for P = 1 (the
+    plain search) .. 32, at the same total budget n / speedup."""
+    from paper_1602_06819_gb300 import inputs
+    W = inputs.PLAIN_D128
+    X = torch.from_numpy(W.initial()).cuda()
+    Q = torch.from_numpy(W.mixture.sample(1024, W.seed_query)).cuda()
+    n, k, nq = X.shape[0], 10, Q.shape[0]
+    for speedup in (4.0, 16.0):
+        for P in (1, 2, 4, 8, 16, 32):
+            if P == 1:
+                Xo, offs = X, torch.tensor([0, n], dtype=torch.int64)
+            else:
+                perm = torch.empty(n, dtype=torch.int64, device="cuda")
+                offs = torch.empty(P + 1, dtype=torch.int64, device="cuda")
+                knn.knn_balanced_kmedoids(X, P, 1.05, 1, 2, 5, order=perm, offsets=offs)
+                Xo = X[perm].contiguous()
+                offs = offs.cpu()
+            cfg = knn.GraphConfig(dim=W.mixture.d, k=k, depth=2, speedup=1.0, expansion=math.inf,
+                                  max_batch=nq, seed=7, capacity=n)
+            g = knn.Graph(cfg, Xo)
+            ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+            g.query(Q, k, 0, ids)
+            truth = ids.clone()
+            g.set_search(speedup, 5.0, "eager")
+            ctr = np.empty((nq, 8), np.int64)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g.query_partitioned(Q, k, 0, offs, ids)          # warm
+            torch.cuda.synchronize()
+            e0.record()
+            g.query_partitioned(Q, k, 0, offs, ids)
+            e1.record()
+            torch.cuda.synchronize()
+            batch_ms = e0.elapsed_time(e1)
+            g.counters(ctr)
+            recall = float((ids[:, :, None] == truth[:, None, :]).any(-1).float().mean().item())
+            one = torch.empty((1, k), dtype=torch.int64, device="cuda")
+            lat = []
+            for i in range(64):
+                e0.record()
+                g.query_partitioned(Q[i:i + 1], k, 10_000 + i, offs, one)
+                e1.record()
+                torch.cuda.synchronize()
+                lat.append(e0.elapsed_time(e1))
+            g.close()
+            lat.sort()
+            _exp_line(experiment="partitions", set="gmm-d128-n100k", n=n, queries=nq, k=k,
+                      speedup=speedup, expansion=5.0, parts=P, recall=recall,
+                      evals_per_query=float(ctr[:, 0].mean()), batch_ms=batch_ms,
+                      single_query_ms_p50=lat[len(lat) // 2], single_query_ms_p99=lat[-1])
+
+
 def main():
     args = parse_args()
     W = pick_workload(args)
@@ -438,7 +503,8 @@ def main():
         kbuild.build()
         from paper_1602_06819_gb300 import knn
         torch.cuda.set_device(0)
-        {"search": run_search_experiment, "depth": run_depth_experiment}[args.experiment](knn, torch, np)
+        {"search": run_search_experiment, "depth": run_depth_experiment,
+         "partitions": run_partition_experiment}[args.experiment](knn, torch, np)
         return
 
     import numpy as np
@@ -459,6 +525,18 @@ def main():
     K, Wm, B = args.steps, args.warmup, W.batch
     n_stream = (K + Wm) * B
     X0 = torch.from_numpy(W.initial()).cuda()
+    order_ms = None
+    if args.order == "kmedoids":
+        # Algorithm 4 as a node ordering: the clusters become contiguous id ranges
+        perm = torch.empty(W.n_init, dtype=torch.int64, device="cuda")
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        o0.record()
+        knn.knn_balanced_kmedoids(X0, kmedoids_clusters(W.n_init), 1.1, 8, 1, W.seed_search, order=perm)
+        o1.record()
+        torch.cuda.synchronize()
+        order_ms = o0.elapsed_time(o1)
+        X0 = X0[perm].contiguous()
     Xs_host = W.mixture.sample(n_stream, W.seed_stream + 1000 * rank)
     Xs = torch.from_numpy(Xs_host).cuda()
     capacity = W.n_init + n_stream
@@ -589,6 +667,7 @@ def main():
                                  "cross": (st1["cross_evals"] - st0["cross_evals"]) / (K * B)},
             "phases_ms_per_step": {p: v / K for p, v in phases.items()},
             "exact_build_ms": exact_ms,
+            "order_ms": order_ms,
             "exact_ground_truth": exact_gt,
             "roofline": {"kernel": f"ignns_search_kernel<{args.storage},{dp}>", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
