@@ -169,6 +169,17 @@ KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_
                                          int64_t *out_ids, float *out_sims, void *stream);
 
 /*
+ * knn_graph_query_batch with one restart stream per query: query i uses
+ * stream 2^63 + query_ids[i] (query_ids: [m] uint64, host or device), so a
+ * query's result depends only on the graph it sees, its vector and its id --
+ * not on the other queries of the call.  Arguments and errors otherwise as
+ * knn_graph_query_batch.
+ */
+KNN_API knn_status knn_graph_query_ids(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                       const uint64_t *query_ids, int64_t *out_ids, float *out_sims,
+                                       void *stream);
+
+/*
  * Partitioned search (Sec. 6, Algorithm 3): every query is searched
  * independently in each of `parts` partitions of the graph, then the k_out
  * most similar of the parts * k_out candidates are kept.  Partition j is
@@ -355,6 +366,74 @@ KNN_API knn_status knn_balanced_kmedoids(const float *X, int64_t n, int32_t dim,
                                          double imbalance, int32_t chunks, int32_t iters,
                                          uint64_t seed, int32_t *out_labels, int64_t *out_medoids,
                                          int64_t *out_order, int64_t *out_offsets, void *stream);
+
+/*
+ * Continuous-batching server over one graph.  A worker thread owns the
+ * graph: it forms device steps from the submitted requests in submission
+ * order, admitting requests while their points fit the step's device slots
+ * (max_step_points) and, for inserts, the graph's capacity; requests that
+ * arrive while steps run join the next step as slots free up.  Two steps
+ * are in flight: the host-to-device copy of step t+1 and the device-to-host
+ * copy of step t-1 overlap step t's kernels (separate copy streams).
+ *
+ * A step runs the searches of all its queries and inserts against the graph
+ * as it stood before the step (epoch E), then commits its inserts (epoch
+ * E+1); searches never overlap an update.  Query point i of request r uses
+ * restart stream 2^63 + r * 2^20 + i, so a query's result is a function of
+ * (epoch, its vector, r, the graph's seed) alone: the same alone as in any
+ * mix.  An insert's search uses its new node id as stream, and its batch
+ * shares the intra-batch merge, so an insert's result depends on the mix
+ * within the method's recall tolerance.
+ */
+typedef struct knn_server knn_server;
+
+typedef struct knn_server_params {
+    int32_t k_out;           /* neighbours returned per query point, 1..k           */
+    int32_t max_step_points; /* points per step, 1..max_batch (0: max_batch)        */
+} knn_server_params;
+
+typedef enum knn_request_kind { KNN_REQ_INSERT = 0, KNN_REQ_QUERY = 1 } knn_request_kind;
+
+typedef struct knn_request_info {
+    int32_t status;     /* KNN_OK, or the error that failed the request             */
+    int32_t kind;       /* knn_request_kind                                          */
+    int64_t m;          /* points                                                    */
+    int64_t epoch;      /* graph version its searches saw (insert steps before it)  */
+    int64_t step;       /* device step that ran it                                   */
+    double queue_ms;    /* submission -> admitted into a step                        */
+    double latency_ms;  /* submission -> results on the host                         */
+} knn_request_info;
+
+typedef struct knn_server_stats {
+    int64_t steps, requests, points, inserts, queries;
+    int64_t epoch;              /* insert steps committed                             */
+    int64_t max_queue;          /* most requests waiting at once                      */
+    double busy_ms;             /* device time of all steps (CUDA events)            */
+} knn_server_stats;
+
+/* Start a server on g (which it then owns until knn_server_destroy: make no
+ * other call on g meanwhile).  Allocates its device slots (two steps of
+ * max_step_points points) and pinned host staging. */
+KNN_API knn_status knn_server_create(knn_graph *g, const knn_server_params *p, knn_server **out);
+
+/* Enqueue a request of m points (vecs: [m, dim] float32 host memory, copied
+ * before returning), 1 <= m <= min(max_step_points, 2^20).  *request_id gets
+ * its id: 0, 1, 2, ... in submission order.  Thread-safe. */
+KNN_API knn_status knn_server_submit(knn_server *s, int32_t kind, const float *vecs, int64_t m,
+                                     uint64_t *request_id);
+
+/* Block until the request has finished, then copy its results to host
+ * memory: a query's ids [m, k_out] int64 and sims [m, k_out] float32, an
+ * insert's new node ids [m] (sims unused).  Each argument is nullable; a
+ * request's results can be taken once.  Thread-safe. */
+KNN_API knn_status knn_server_wait(knn_server *s, uint64_t request_id, int64_t *out_ids,
+                                   float *out_sims, knn_request_info *info);
+
+KNN_API knn_status knn_server_get_stats(knn_server *s, knn_server_stats *out);
+
+/* Finish every submitted request, stop the worker and free the server (the
+ * graph stays alive and usable again). */
+KNN_API void knn_server_destroy(knn_server *s);
 
 /* Message of the last failed call on this thread ("" if none). */
 KNN_API const char *knn_last_error(void);

@@ -61,6 +61,7 @@ struct knn_graph {
     uint64_t *keys_final = nullptr;
     long long *counters = nullptr;
     uint64_t *keys_merge = nullptr;      // partitioned queries: merged candidates [M][KT]
+    uint64_t *qstreams = nullptr;        // per-query restart streams [M] (knn_graph_query_ids)
     long long *counters_q = nullptr;     // partitioned queries: per-query counters [M][NCTR]
     int64_t *part_off = nullptr;         // [KNN_MAX_PARTS + 1]
     int64_t *part_live = nullptr;        // [KNN_MAX_PARTS]
@@ -103,6 +104,10 @@ static knn_status fail(knn_status st, const char *fmt, ...) {
     va_end(ap);
     g_last_error = buf;
     return st;
+}
+
+GraphShape knn::graph_shape(const knn_graph *g) {
+    return GraphShape{g->p.dim, g->p.k, g->p.max_batch, g->n, g->p.capacity};
 }
 
 knn_status knn::record_error(knn_status st, const char *msg) {
@@ -251,7 +256,8 @@ static const uint8_t *searched_rows(const knn_graph *g) {
 // the best k_out keys of each item in g->keys_final (screening forms) or
 // g->keys_search (FP32), and returns which.
 static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int k_out,
-                             uint64_t stream_base, cudaStream_t s, const uint64_t **keys_out) {
+                             uint64_t stream_base, cudaStream_t s, const uint64_t **keys_out,
+                             const uint64_t *streams = nullptr) {
     const bool screening = g->p.storage != KNN_STORAGE_FP32;
     const int KT = screening ? g->p.rescore_mult * k_out : k_out;
     if (!search_visited_on_chip((uint32_t)g->n))
@@ -283,6 +289,7 @@ static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int 
     a.climb = g->climb;
     a.vis_n = (uint32_t)g->n;
     a.speedup = g->p.speedup;
+    a.streams = streams;
     CU(launch_search(g->p.storage, g->dp, a, s));
     g->last_counters_src = g->counters;
     ++g->launches;
@@ -392,7 +399,8 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
                   (size_t)M * g->vwords * 4 + (size_t)M * DP * 4 + (size_t)M * p.dim * 4 +
                   (size_t)M * g->KT * 8 + (size_t)M * K * 8 + (size_t)M * NCTR * 8 +
                   (size_t)g->offer_cap * 16 + (size_t)M * K * 12 + (size_t)M * levels * 4 +
-                  (size_t)M * g->KT * 8 + (size_t)M * NCTR * 8 + (size_t)(2 * KNN_MAX_PARTS + 1) * 8;
+                  (size_t)M * g->KT * 8 + (size_t)M * NCTR * 8 + (size_t)(2 * KNN_MAX_PARTS + 1) * 8 +
+                  (size_t)M * 8;
     if (p.storage == KNN_STORAGE_BF16) need += (size_t)C * DP * 2;
     if (p.storage == KNN_STORAGE_FP8_E4M3) need += (size_t)C * DP + (size_t)C * 4;
     size_t free_b = 0, total_b = 0;
@@ -423,6 +431,7 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
     ALLOC(keys_final, M * K)
     ALLOC(counters, M * NCTR)
     ALLOC(keys_merge, M * g->KT)
+    ALLOC(qstreams, M)
     ALLOC(counters_q, M * NCTR)
     ALLOC(part_off, KNN_MAX_PARTS + 1)
     ALLOC(part_live, KNN_MAX_PARTS)
@@ -653,6 +662,36 @@ KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_
     phase_mark(g, KNN_PHASE_SEARCH, s);
     const uint64_t *keys = nullptr;
     TRY(run_search(g, g->qbuf, m, k_out, (1ull << 63) + query_id0, s, &keys));
+    phase_mark(g, KNN_PHASE_CROSS, s);
+    for (int ph = KNN_PHASE_CROSS + 1; ph <= KNN_NUM_PHASES; ++ph) phase_mark(g, ph, s);
+    bool synced = false;
+    TRY(emit_keys(g, keys, m, k_out, k_out, out_ids, out_sims, s, &synced));
+    g->queries += m;
+    g->last_m = m;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_query_ids(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                       const uint64_t *query_ids, int64_t *out_ids, float *out_sims,
+                                       void *stream) {
+    if (!g || !vecs || !out_ids || !query_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (m < 1 || m > g->p.max_batch)
+        return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
+    if (k_out < 1 || k_out > g->p.k) return fail(KNN_ERR_INVALID_ARG, "k_out outside 1..k");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    phase_begin_call(g);
+    phase_mark(g, KNN_PHASE_STORE, s);
+    TRY(append_rows(g, vecs, m, 0, g->qbuf, false, s));
+    // restart stream of query i: 2^63 + query_ids[i], added on the device
+    CU(cudaMemcpyAsync(g->qstreams, query_ids, (size_t)m * 8, cudaMemcpyDefault, s));
+    CU(launch_add_u64(g->qstreams, 1ull << 63, m, s));
+    ++g->launches;
+    g->phase_ran[KNN_PHASE_STORE] = true;
+    phase_mark(g, KNN_PHASE_SEARCH, s);
+    const uint64_t *keys = nullptr;
+    TRY(run_search(g, g->qbuf, m, k_out, 0, s, &keys, g->qstreams));
     phase_mark(g, KNN_PHASE_CROSS, s);
     for (int ph = KNN_PHASE_CROSS + 1; ph <= KNN_NUM_PHASES; ++ph) phase_mark(g, ph, s);
     bool synced = false;

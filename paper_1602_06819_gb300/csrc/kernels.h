@@ -72,6 +72,7 @@ struct SearchArgs {
     const int64_t *part_live = nullptr;  // [parts] live nodes of each partition
     double speedup = 1.0;
     uint32_t vis_n = 0;                  // bits of one visited set (n, or the largest partition)
+    const uint64_t *streams = nullptr;   // nullable: restart stream of query i (replaces stream_base + i)
 };
 constexpr uint64_t PART_STREAM_STEP = 1ull << 56;
 
@@ -179,6 +180,9 @@ cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned 
 cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,
                                  int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s);
 
+// p[i] += v for i < m (misc.cu)
+cudaError_t launch_add_u64(uint64_t *p, uint64_t v, int64_t m, cudaStream_t s);
+
 // partitioned search: per query, the k_keep best of its parts * k_keep
 // candidate keys ([m * parts][k_keep] -> [m][k_keep]) and the sums of its
 // searches' counters ([m * parts][NCTR] -> [m][NCTR]) (misc.cu)
@@ -200,6 +204,13 @@ cudaError_t launch_kmed_sort(const int32_t *labels, int64_t n, int p, void *scra
 // medoid of every non-empty cluster (members order[offsets[m] .. offsets[m+1]))
 cudaError_t launch_kmed_update(int dp, const float *X, const int64_t *order, const int64_t *offsets, int p,
                                int64_t *medoids, cudaStream_t s);
+
+// shape of a graph for the server (graph.cu)
+struct GraphShape {
+    int dim, k, max_batch;
+    int64_t n, capacity;
+};
+GraphShape graph_shape(const knn_graph *g);
 
 // set the calling thread's knn_last_error() message (graph.cu)
 knn_status record_error(knn_status st, const char *msg);

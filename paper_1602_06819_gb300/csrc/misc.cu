@@ -153,6 +153,17 @@ cudaError_t launch_merge_parts(const uint64_t *keys, int32_t m, int32_t parts, i
     return cudaGetLastError();
 }
 
+__global__ void add_u64_kernel(uint64_t *p, uint64_t v, int64_t m) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) p[t] += v;
+}
+
+cudaError_t launch_add_u64(uint64_t *p, uint64_t v, int64_t m, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    add_u64_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p, v, m);
+    return cudaGetLastError();
+}
+
 __global__ void fill_ids_kernel(int64_t *out, int64_t first, int64_t m) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m) out[t] = first + t;

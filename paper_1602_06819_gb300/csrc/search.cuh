@@ -142,8 +142,8 @@ ignns_search_kernel(const SearchArgs a) {
         } else {
             vis.bits = a.visited + (size_t)sw * a.vwords;
         }
-        const uint64_t rkey =
-            restart_key(a.seed, a.stream_base + (uint64_t)qi + (uint64_t)part * PART_STREAM_STEP);
+        const uint64_t stream = a.streams ? a.streams[qi] : a.stream_base + (uint64_t)qi;
+        const uint64_t rkey = restart_key(a.seed, stream + (uint64_t)part * PART_STREAM_STEP);
 
         WarpTop<T> top;
         top.init(a.KT);

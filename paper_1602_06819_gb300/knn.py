@@ -45,11 +45,16 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
 
 # Every symbol include/knn_graph.h declares.
 EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
-            "knn_graph_query_partitioned", "knn_graph_remove", "knn_graph_get_edges",
+            "knn_graph_query_ids", "knn_graph_query_partitioned", "knn_graph_remove", "knn_graph_get_edges",
             "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
             "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
-            "knn_balanced_kmedoids", "knn_search_noalloc", "knn_last_error", "knn_version")
+            "knn_balanced_kmedoids", "knn_server_create", "knn_server_submit", "knn_server_wait",
+            "knn_server_get_stats", "knn_server_destroy", "knn_search_noalloc", "knn_last_error",
+            "knn_version")
+
+KNN_REQ_INSERT = 0
+KNN_REQ_QUERY = 1
 
 EXACT_PATHS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
 
@@ -79,6 +84,28 @@ class KnnExactInfo(ctypes.Structure):
                 ("rows_redone", ctypes.c_int64)]
 
 
+class KnnServerParams(ctypes.Structure):
+    _fields_ = [("k_out", ctypes.c_int32), ("max_step_points", ctypes.c_int32)]
+
+
+class KnnRequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("epoch", ctypes.c_int64), ("step", ctypes.c_int64), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class KnnServerStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("requests", ctypes.c_int64), ("points", ctypes.c_int64),
+                ("inserts", ctypes.c_int64), ("queries", ctypes.c_int64), ("epoch", ctypes.c_int64),
+                ("max_queue", ctypes.c_int64), ("busy_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class KnnError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: status {status}: {msg}")
@@ -97,6 +124,7 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_insert_batch": (I32, [P, P, I64, P, P, P]),
         "knn_graph_query_batch": (I32, [P, P, I64, I32, U64, P, P, P]),
         "knn_graph_query_partitioned": (I32, [P, P, I64, I32, U64, P, I32, P, P, P]),
+        "knn_graph_query_ids": (I32, [P, P, I64, I32, P, P, P, P]),
         "knn_graph_remove": (I32, [P, P, I64, P]),
         "knn_graph_get_edges": (I32, [P, P, P, I64, ctypes.POINTER(I64), P]),
         "knn_graph_last_counters": (I32, [P, P, I64, P]),
@@ -106,6 +134,11 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_destroy": (None, [P]),
         "knn_exact_graph": (I32, [P, I64, I32, I32, P, P, P]),
         "knn_exact_set_path": (I32, [I32]),
+        "knn_server_create": (I32, [P, ctypes.POINTER(KnnServerParams), ctypes.POINTER(P)]),
+        "knn_server_submit": (I32, [P, I32, P, I64, ctypes.POINTER(U64)]),
+        "knn_server_wait": (I32, [P, U64, P, P, ctypes.POINTER(KnnRequestInfo)]),
+        "knn_server_get_stats": (I32, [P, ctypes.POINTER(KnnServerStats)]),
+        "knn_server_destroy": (None, [P]),
         "knn_balanced_kmedoids": (I32, [P, I64, I32, I32, ctypes.c_double, I32, I32, U64, P, P, P, P, P]),
         "knn_graph_set_search": (I32, [P, ctypes.c_double, ctypes.c_double, I32]),
         "knn_exact_last_info": (I32, [ctypes.POINTER(KnnExactInfo)]),
@@ -193,6 +226,17 @@ def knn_graph_query_batch(g, vecs, k_out: int, query_id0: int, out_ids, out_sims
     _check_dtype(out_sims, "float32", "out_sims")
     _check(lib.knn_graph_query_batch(g, _ptr(vecs), vecs.shape[0], k_out, query_id0, _ptr(out_ids),
                                      _ptr(out_sims), _stream(stream)), "knn_graph_query_batch")
+
+
+def knn_graph_query_ids(g, vecs, k_out: int, query_ids, out_ids, out_sims=None, stream=None) -> None:
+    """Queries with their own restart streams 2^63 + query_ids[i] (uint64)."""
+    _check_dtype(vecs, "float32", "vecs")
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_sims, "float32", "out_sims")
+    if str(query_ids.dtype) not in ("uint64", "torch.uint64", "int64", "torch.int64"):
+        raise TypeError("query_ids must be 64-bit integers")
+    _check(lib.knn_graph_query_ids(g, _ptr(vecs), vecs.shape[0], k_out, _ptr(query_ids), _ptr(out_ids),
+                                   _ptr(out_sims), _stream(stream)), "knn_graph_query_ids")
 
 
 def knn_graph_query_partitioned(g, vecs, k_out: int, query_id0: int, part_offsets, out_ids,
@@ -350,6 +394,9 @@ class Graph:
     def query(self, vecs, k_out, query_id0, out_ids, out_sims=None, stream=None):
         knn_graph_query_batch(self.handle, vecs, k_out, query_id0, out_ids, out_sims, stream)
 
+    def query_ids(self, vecs, k_out, query_ids, out_ids, out_sims=None, stream=None):
+        knn_graph_query_ids(self.handle, vecs, k_out, query_ids, out_ids, out_sims, stream)
+
     def query_partitioned(self, vecs, k_out, query_id0, part_offsets, out_ids, out_sims=None,
                           stream=None):
         knn_graph_query_partitioned(self.handle, vecs, k_out, query_id0, part_offsets, out_ids,
@@ -392,3 +439,53 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching server over a Graph (knn_server_*).  The graph is
+    owned by the server's worker until close(); submit() and wait() may be
+    called from any thread (the C calls release the GIL)."""
+
+    def __init__(self, graph: "Graph", k_out: int, max_step_points: int = 0):
+        self.graph = graph
+        self.k_out = k_out
+        self.dim = graph.cfg.dim
+        h = ctypes.c_void_p()
+        _check(lib.knn_server_create(graph.handle, ctypes.byref(KnnServerParams(k_out, max_step_points)),
+                                     ctypes.byref(h)), "knn_server_create")
+        self.handle = h
+
+    def submit(self, kind: int, vecs: np.ndarray) -> int:
+        """Enqueue a request of host float32 points [m, dim]; returns its id."""
+        v = np.ascontiguousarray(vecs, dtype=np.float32)
+        rid = ctypes.c_uint64()
+        _check(lib.knn_server_submit(self.handle, kind, v.ctypes.data, v.shape[0], ctypes.byref(rid)),
+               "knn_server_submit")
+        return rid.value
+
+    def wait(self, request_id: int, m: int, kind: int):
+        """Block until done: (ids, sims or None, info dict).  A query's ids and
+        sims are [m, k_out]; an insert's ids are its new node ids [m]."""
+        ids = np.empty((m, self.k_out) if kind == KNN_REQ_QUERY else m, np.int64)
+        sims = np.empty((m, self.k_out), np.float32) if kind == KNN_REQ_QUERY else None
+        info = KnnRequestInfo()
+        _check(lib.knn_server_wait(self.handle, request_id, ids.ctypes.data,
+                                   None if sims is None else sims.ctypes.data, ctypes.byref(info)),
+               "knn_server_wait")
+        return ids, sims, info.as_dict()
+
+    def stats(self) -> dict:
+        out = KnnServerStats()
+        _check(lib.knn_server_get_stats(self.handle, ctypes.byref(out)), "knn_server_get_stats")
+        return out.as_dict()
+
+    def close(self):
+        if self.handle:
+            lib.knn_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
