@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--order", default="none", choices=("none", "kmedoids"),
                     help="store the initial points in the order of their balanced k-medoids "
                          "clusters (Algorithm 4; n/1000 clusters) before building the graph")
-    ap.add_argument("--experiment", default=None, choices=("search", "depth", "partitions"),
+    ap.add_argument("--experiment", default=None, choices=("search", "depth", "partitions", "serving"),
                     help="instead of the benchmark line: the search sweeps (expansion e; "
                          "iGNNS against GNNS at equal evaluations) or the DEPTH sweep, "
                          "one JSON line per point")
@@ -490,6 +490,95 @@ def run_partition_experiment(knn, torch, np):
                       single_query_ms_p50=lat[len(lat) // 2], single_query_ms_p99=lat[-1])
 
 
+def run_serving_experiment(knn, torch, np):
+    """The serving pattern: Poisson arrivals of requests (insert : query =
+    1 : 4, 1..512 points each, uniform) into the continuous-batching server
+    over one growing graph (1,000,000 initial points, d = 128, k = 10,
+    BF16 screening with FP32 re-score, speedup 4, e = 5); for each arrival
+    rate lambda, about 15 s of traffic: completed points/s, p50/p99 request
+    latency (submission to results on the host) and the mean step.  The same
+    sweep on the plain FP32 path for comparison; recall@10 of 256 queries
+    against exhaustive search on the final graph of each run."""
+    from paper_1602_06819_gb300 import inputs
+    import threading
+    mix = inputs.Mixture(d=128, components=1000, half_width=20.0, sigma=1.0, seed=51)
+    n0, k, seconds = 1_000_000, 10, 15.0
+    pool = mix.sample(600_000, 52)
+    Qr = mix.sample(256, 53)
+    rng = np.random.default_rng(54)
+    for storage, lams in (("bf16", (10, 20, 30, 40, 60, 80)), ("fp32", (10, 20, 30, 40))):
+        st = {"fp32": knn.KNN_STORAGE_FP32, "bf16": knn.KNN_STORAGE_BF16}[storage]
+        cfg = knn.GraphConfig(dim=128, k=k, depth=2, storage=st, speedup=4.0, expansion=5.0,
+                              rescore_mult=4, max_batch=1024, seed=9, capacity=n0 + pool.shape[0])
+        g = knn.Graph(cfg, torch.from_numpy(mix.sample(n0, 50)).cuda())
+        used = 0
+        for lam in lams:
+            srv = knn.Server(g, k, 1024)
+            pending = []
+            lock = threading.Lock()
+            done_evt = threading.Event()
+            lat, sizes = [], []
+
+            def waiter():
+                while True:
+                    with lock:
+                        item = pending.pop(0) if pending else None
+                    if item is None:
+                        if done_evt.is_set():
+                            return
+                        time.sleep(0.0005)
+                        continue
+                    rid, m, kind = item
+                    _, _, info = srv.wait(rid, m, kind)
+                    lat.append(info["latency_ms"])
+                    sizes.append(m)
+
+            th = threading.Thread(target=waiter)
+            th.start()
+            t_start = time.perf_counter()
+            t_next = t_start
+            nsub = 0
+            while t_next - t_start < seconds:
+                now = time.perf_counter()
+                if now < t_next:
+                    time.sleep(min(t_next - now, 0.002))
+                    continue
+                m = int(rng.integers(1, 513))
+                kind = knn.KNN_REQ_INSERT if rng.random() < 0.2 else knn.KNN_REQ_QUERY
+                if used + m > pool.shape[0]:
+                    used = 0
+                vecs = pool[used:used + m]
+                used += m
+                rid = srv.submit(kind, vecs)
+                with lock:
+                    pending.append((rid, m, kind))
+                nsub += 1
+                t_next += rng.exponential(1.0 / lam)
+            done_evt.set()
+            th.join()
+            wall = time.perf_counter() - t_start
+            stats = srv.stats()
+            srv.close()
+            lat.sort()
+            _exp_line(experiment="serving", storage=storage, lam_requests_per_s=lam, requests=nsub,
+                      points_per_s=sum(sizes) / wall, offered_points_per_s=lam * 256.5,
+                      p50_ms=lat[len(lat) // 2], p99_ms=lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                      steps=stats["steps"], mean_step_points=stats["points"] / max(1, stats["steps"]),
+                      gpu_busy_frac=stats["busy_ms"] / (wall * 1e3), graph_n=g.stats()["n"],
+                      max_queue=stats["max_queue"], seconds=wall)
+        # recall@10 of queries on the final graph against exhaustive search
+        Q = torch.from_numpy(Qr).cuda()
+        ids = torch.empty((256, k), dtype=torch.int64, device="cuda")
+        g.query(Q, k, 0, ids)
+        got = ids.clone()
+        g.set_search(1.0, math.inf, "eager")
+        g.query(Q, k, 0, ids)
+        torch.cuda.synchronize()
+        rec = float((got[:, :, None] == ids[:, None, :]).any(-1).float().mean().item())
+        _exp_line(experiment="serving_recall", storage=storage, graph_n=g.stats()["n"], recall_at_10=rec)
+        g.close()
+
+
 def main():
     args = parse_args()
     W = pick_workload(args)
@@ -504,7 +593,8 @@ def main():
         from paper_1602_06819_gb300 import knn
         torch.cuda.set_device(0)
         {"search": run_search_experiment, "depth": run_depth_experiment,
-         "partitions": run_partition_experiment}[args.experiment](knn, torch, np)
+         "partitions": run_partition_experiment, "serving": run_serving_experiment}[args.experiment](
+            knn, torch, np)
         return
 
     import numpy as np

@@ -110,6 +110,11 @@ GraphShape knn::graph_shape(const knn_graph *g) {
     return GraphShape{g->p.dim, g->p.k, g->p.max_batch, g->n, g->p.capacity};
 }
 
+void knn::graph_forget_stream(knn_graph *g, cudaStream_t s) {
+    cudaStreamSynchronize(s);
+    if (g->last_stream == s) g->last_stream = nullptr;
+}
+
 knn_status knn::record_error(knn_status st, const char *msg) {
     g_last_error = msg;
     return st;

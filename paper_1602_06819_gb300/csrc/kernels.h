@@ -211,6 +211,9 @@ struct GraphShape {
     int64_t n, capacity;
 };
 GraphShape graph_shape(const knn_graph *g);
+// a stream the caller is about to destroy: synchronise it and stop using it
+// as the graph's last stream (graph.cu)
+void graph_forget_stream(knn_graph *g, cudaStream_t s);
 
 // set the calling thread's knn_last_error() message (graph.cu)
 knn_status record_error(knn_status st, const char *msg);

@@ -358,6 +358,7 @@ KNN_API void knn_server_destroy(knn_server *s) {
         for (cudaEvent_t ev : {sl.uploaded, sl.computed, sl.downloaded, sl.t0, sl.t1})
             if (ev) cudaEventDestroy(ev);
     }
+    if (s->comp) graph_forget_stream(s->g, s->comp);
     for (cudaStream_t st : {s->up, s->comp, s->down})
         if (st) cudaStreamDestroy(st);
     delete s;

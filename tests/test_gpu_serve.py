@@ -84,6 +84,7 @@ def test_mixed_requests_and_replay(knn):
     try:
         results, stats = serve(knn, g, reqs)
         final = edges(knn, g, N0 + n_ins)
+        assert g.stats()["n"] == N0 + n_ins   # the graph is usable again after the server
     finally:
         g.close()
     assert len(results) == len(reqs) and all(r[3]["status"] == 0 for r in results.values())
