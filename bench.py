@@ -61,7 +61,8 @@ def parse_args():
     ap.add_argument("--order", default="none", choices=("none", "kmedoids"),
                     help="store the initial points in the order of their balanced k-medoids "
                          "clusters (Algorithm 4; n/1000 clusters) before building the graph")
-    ap.add_argument("--experiment", default=None, choices=("search", "depth", "partitions", "serving"),
+    ap.add_argument("--experiment", default=None,
+                    choices=("search", "depth", "partitions", "serving", "batching"),
                     help="instead of the benchmark line: the search sweeps (expansion e; "
                          "iGNNS against GNNS at equal evaluations) or the DEPTH sweep, "
                          "one JSON line per point")
@@ -579,6 +580,69 @@ def run_serving_experiment(knn, torch, np):
         g.close()
 
 
+def run_batching_experiment(knn, torch, np):
+    """The batching pattern: 64 independent graphs of uneven sizes (n
+    log-uniform in 1,000 .. 200,000, d = 64 FP32, k = 10, each its own
+    10-component mixture with means in [-10, 10]^64, sigma 1) in one arena,
+    receiving steps of 16..4,096 items (insert : query = 1 : 1, graphs
+    uniform).  The search launch width and step size cap are autotuned on
+    query-only steps; then the same 60 steps run with the step's launch
+    sequence replayed from a CUDA graph and run directly."""
+    from paper_1602_06819_gb300 import inputs
+    rng = np.random.default_rng(61)
+    G, k, n_steps = 64, 10, 60
+    sizes = np.floor(10 ** rng.uniform(3, np.log10(2e5), G)).astype(np.int64)
+    mixes = [inputs.Mixture(d=64, components=10, half_width=10.0, sigma=1.0, seed=100 + i) for i in range(G)]
+    inits = np.concatenate([mixes[i].sample(int(sizes[i]), 1) for i in range(G)])
+    caps = sizes + 4096
+    steps, qid = [], 0
+    for t in range(n_steps):
+        m = int(rng.integers(16, 4097))
+        graph = rng.integers(0, G, m).astype(np.int32)
+        kind = (rng.random(m) < 0.5).astype(np.int32)
+        vecs = np.empty((m, 64), np.float32)
+        for gi in np.unique(graph):
+            idx = np.flatnonzero(graph == gi)
+            vecs[idx] = mixes[gi].sample(idx.size, 1000 + 97 * t + int(gi))
+        steps.append((vecs, graph, kind, np.arange(qid, qid + m, dtype=np.uint64)))
+        qid += m
+    sample_g = rng.integers(0, G, 4096).astype(np.int32)
+    sample_v = np.stack([mixes[gi].sample(1, 5_000_000 + i)[0] for i, gi in enumerate(sample_g)])
+    sample = (sample_v, sample_g, np.arange(4096, dtype=np.uint64))
+    X0 = torch.from_numpy(inits).cuda()
+    tuned = None
+    for use_graph in (True, False):
+        cfg = knn.GraphConfig(dim=64, k=k, depth=2, speedup=4.0, expansion=5.0, max_batch=4096, seed=3)
+        t0 = time.perf_counter()
+        mg = knn.MultiGraph(cfg, sizes, caps, X0, use_graph=use_graph)
+        build_s = time.perf_counter() - t0
+        if tuned is None:
+            tuned = mg.autotune(sample)
+            _exp_line(experiment="batching_autotune", **tuned["best"],
+                      tried=[{kk: (round(v) if kk == "items_per_s" else v) for kk, v in r.items()}
+                             for r in tuned["tried"]])
+        else:
+            mg.set_launch(tuned["best"]["search_warps"])
+        cap = tuned["best"]["step_cap"]
+        for vecs, graph, kind, qids in steps[:3]:   # warm-up (and capture)
+            mg.step_many(vecs, graph, kind, qids, cap)
+        lat, items = [], 0
+        t0 = time.perf_counter()
+        for vecs, graph, kind, qids in steps[3:]:
+            a = time.perf_counter()
+            mg.step_many(vecs, graph, kind, qids, cap)
+            lat.append((time.perf_counter() - a) * 1e3)
+            items += len(graph)
+        wall = time.perf_counter() - t0
+        total_n = sum(mg.size(i)[0] for i in range(G))
+        mg.close()
+        lat.sort()
+        _exp_line(experiment="batching", graphs=G, d=64, k=k, sizes_min=int(sizes.min()), sizes_max=int(sizes.max()),
+                  nodes_total=int(total_n), use_cuda_graph=use_graph, search_warps=tuned["best"]["search_warps"],
+                  step_cap=cap, steps=len(lat), items_per_s=items / wall, step_ms_p50=lat[len(lat) // 2],
+                  step_ms_p99=lat[-1], mean_items_per_step=items / len(lat), build_s=build_s)
+
+
 def main():
     args = parse_args()
     W = pick_workload(args)
@@ -593,7 +657,8 @@ def main():
         from paper_1602_06819_gb300 import knn
         torch.cuda.set_device(0)
         {"search": run_search_experiment, "depth": run_depth_experiment,
-         "partitions": run_partition_experiment, "serving": run_serving_experiment}[args.experiment](
+         "partitions": run_partition_experiment, "serving": run_serving_experiment,
+         "batching": run_batching_experiment}[args.experiment](
             knn, torch, np)
         return
 

@@ -435,6 +435,50 @@ KNN_API knn_status knn_server_get_stats(knn_server *s, knn_server_stats *out);
  * graph stays alive and usable again). */
 KNN_API void knn_server_destroy(knn_server *s);
 
+/*
+ * Several independent graphs served together: G graphs of uneven sizes live
+ * in one device arena (graph i owns capacity[i] node slots), and a step
+ * takes a mixed batch of insert and query items for any of them.  Every
+ * item's search runs against its own graph as it stood before the step
+ * (budget max(1, floor(n_i / speedup)), restart draws among its nodes), the
+ * inserts of one graph meet each other in the intra-batch merge and Update
+ * offers them to that graph's older nodes only -- so each graph evolves
+ * exactly as a knn_graph given the same items would.  All the step's kernels
+ * run with fixed grids and read the step's sizes from device tables, so one
+ * launch sequence serves every step; with use_graph it is captured once into
+ * a CUDA graph (at the second step) and replayed.
+ *
+ * knn_multi_create: params as knn_graph_create (max_batch = items per step;
+ * capacity is ignored); n_init, capacity: [graphs] with k+1 <= n_init[i] <=
+ * capacity[i], sum of capacities < 2^31; init_vecs: [sum n_init, dim] float32
+ * host or device, graph after graph; each initial graph is exact.
+ *
+ * knn_multi_step: m items (1..max_batch), all host memory: vecs [m, dim]
+ * float32, graph [m] int32, kind [m] int32 (knn_request_kind), query_ids [m]
+ * uint64 (used for queries: stream 2^63 + id).  out_ids [m, k] int64: a
+ * query's k best (ids local to its graph), an insert's new local id in
+ * column 0 (-1 after); out_sims [m, k] float32 (nullable; 0 for inserts).
+ * Returns when the outputs are written.  KNN_ERR_CAPACITY if a graph would
+ * overflow (nothing is done).
+ */
+typedef struct knn_multi knn_multi;
+
+KNN_API knn_status knn_multi_create(const knn_params *params, int32_t graphs, const int64_t *n_init,
+                                    const int64_t *capacity, const float *init_vecs, int32_t use_graph,
+                                    void *stream, knn_multi **out);
+KNN_API knn_status knn_multi_step(knn_multi *mg, const float *vecs, const int32_t *graph,
+                                  const int32_t *kind, const uint64_t *query_ids, int64_t m,
+                                  int64_t *out_ids, float *out_sims, void *stream);
+/* Warps of the search launch of later steps (0: one per item slot, i.e.
+ * max_batch).  The search loops over the step's items with that many warps;
+ * fewer than the items makes the launch persistent.  For the autotuner. */
+KNN_API knn_status knn_multi_set_launch(knn_multi *mg, int32_t search_warps);
+/* Nodes and capacity of graph `graph`. */
+KNN_API knn_status knn_multi_graph_size(knn_multi *mg, int32_t graph, int64_t *n, int64_t *capacity);
+/* Lists of graph `graph`: out_ids [n, k] int64 local ids (host or device). */
+KNN_API knn_status knn_multi_get_edges(knn_multi *mg, int32_t graph, int64_t *out_ids, void *stream);
+KNN_API void knn_multi_destroy(knn_multi *mg);
+
 /* Message of the last failed call on this thread ("" if none). */
 KNN_API const char *knn_last_error(void);
 

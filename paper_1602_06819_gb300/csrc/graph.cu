@@ -1096,3 +1096,419 @@ KNN_API knn_status knn_exact_last_info(knn_exact_info *out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Several graphs in one arena (knn_multi_*)
+// ---------------------------------------------------------------------------
+struct knn_multi {
+    knn_graph *g = nullptr;  // the arena: every graph's rows, lists and the step buffers
+    int G = 0;
+    std::vector<uint32_t> lo, cap;
+    std::vector<int64_t> n;
+    int64_t M = 0;           // items per step
+    uint32_t cap_max = 0;
+    bool use_graph = false;
+    // device tables of a step, uploaded from one pinned block
+    uint8_t *h_meta = nullptr, *d_meta = nullptr;
+    size_t meta_bytes = 0;
+    int32_t *d_counts = nullptr;  // m_all, m_ins, m_q
+    int32_t *d_item_seg = nullptr;
+    uint32_t *d_lo = nullptr, *d_n = nullptr;
+    int32_t *d_first = nullptr, *d_perm = nullptr;
+    uint64_t *d_streams = nullptr;
+    float *h_vecs = nullptr, *d_vecs = nullptr;
+    int64_t *d_out = nullptr, *h_out = nullptr;
+    float *d_sims = nullptr, *h_sims = nullptr;
+    int32_t search_warps = 0;            // warps of the search launch (0: max_batch)
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t exec_stream = nullptr;  // a CUDA graph is captured on and replayed from its own stream
+    cudaEvent_t joined = nullptr;
+    int64_t steps = 0;
+};
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// The step's kernels, reading every size from the device tables; the same
+// sequence serves every step (and is what a CUDA graph captures).
+static knn_status multi_launch(knn_multi *mg, cudaStream_t s) {
+    knn_graph *g = mg->g;
+    const int K = g->p.k, dp = g->dp, M = (int)mg->M;
+    const bool screening = g->p.storage != KNN_STORAGE_FP32;
+    const int KT = screening ? g->p.rescore_mult * K : K;
+    const int64_t vwords = (mg->cap_max + 31) / 32;
+    Segments all{mg->d_item_seg, mg->d_lo, mg->d_n, mg->d_first, mg->d_counts};
+    Segments ins{mg->d_item_seg, mg->d_lo, mg->d_n, mg->d_first, mg->d_counts + 1};
+    const int grid = g->sm_count * 4;
+    CU(launch_multi_append(mg->d_vecs, mg->d_counts, ins, g->p.dim, dp, g->qbuf, g->X, g->Xb, g->X8, g->scale, grid,
+                           s));
+    if (!search_visited_on_chip(mg->cap_max))
+        CU(cudaMemsetAsync(g->visited, 0, (size_t)M * vwords * sizeof(uint32_t), s));
+    SearchArgs a{};
+    a.rows = searched_rows(g);
+    a.row_scale = g->scale;
+    a.nbr = g->nbr_ids;
+    a.removed = g->removed;
+    a.queries = g->qbuf;
+    a.q_stride = dp;
+    a.visited = g->visited;
+    a.vwords = vwords;
+    a.out_keys = g->keys_search;
+    a.counters = g->counters;
+    a.totals = g->totals;
+    a.m = mg->search_warps > 0 ? mg->search_warps : M;  // warps launched; the items come from the table
+    a.k = K;
+    a.KT = KT;
+    a.seed = g->p.seed;
+    const double e = g->p.expansion;
+    a.discard = (e > 0.0 && std::isfinite(e)) ? 1 : 0;
+    a.expansion = a.discard ? (float)e : 1.0f;
+    a.climb = g->climb;
+    a.speedup = g->p.speedup;
+    a.vis_n = mg->cap_max;
+    a.streams = mg->d_streams;
+    a.seg = all;
+    CU(launch_search(g->p.storage, dp, a, s));
+    const uint64_t *keys = g->keys_search;
+    if (screening) {
+        RescoreArgs r{};
+        r.rows = g->X;
+        r.queries = g->qbuf;
+        r.q_stride = dp;
+        r.cand_keys = g->keys_search;
+        r.out_keys = g->keys_final;
+        r.totals = g->totals;
+        r.m = M;
+        r.KT = KT;
+        r.k_out = K;
+        r.m_dev = mg->d_counts;
+        CU(launch_rescore(dp, r, s));
+        keys = g->keys_final;
+    }
+    CrossArgs ca{};
+    ca.rows = g->X;
+    ca.in_keys = keys;
+    ca.nbr_ids = g->nbr_ids;
+    ca.nbr_d2 = g->nbr_d2;
+    ca.totals = g->totals;
+    ca.m = M;
+    ca.k = K;
+    ca.seg = ins;
+    CU(launch_cross(dp, ca, s));
+    CU(cudaMemsetAsync(g->small, 0, 2 * sizeof(unsigned), s));
+    UpdateArgs ua{};
+    ua.rows = g->X;
+    ua.nbr_ids = g->nbr_ids;
+    ua.nbr_d2 = g->nbr_d2;
+    ua.removed = g->removed;
+    ua.head = g->head;
+    ua.offer_key = g->offer_key;
+    ua.offer_next = g->offer_next;
+    ua.touched = g->touched;
+    ua.offer_count = g->small + 0;
+    ua.touched_count = g->small + 1;
+    ua.offer_cap = g->offer_cap;
+    ua.error_flags = g->small + 2;
+    ua.counters = g->counters;
+    ua.totals = g->totals;
+    ua.m = M;
+    ua.k = K;
+    ua.depth = g->p.depth;
+    ua.frontier = g->frontier;
+    ua.frontier_cap = g->frontier_cap;
+    ua.seen = g->visited;
+    ua.seen_words = vwords;
+    ua.seg = ins;
+    if (ua.depth >= 2 && !update_seen_on_chip(ua.seen_words))
+        CU(cudaMemsetAsync(g->visited, 0, (size_t)M * ua.seen_words * sizeof(uint32_t), s));
+    CU(launch_update(dp, ua, s));
+    MergeArgs ma{};
+    ma.nbr_ids = g->nbr_ids;
+    ma.nbr_d2 = g->nbr_d2;
+    ma.head = g->head;
+    ma.offer_key = g->offer_key;
+    ma.offer_next = g->offer_next;
+    ma.touched = g->touched;
+    ma.touched_count = g->small + 1;
+    ma.offer_count = g->small + 0;
+    ma.totals = g->totals;
+    ma.k = K;
+    CU(launch_merge(ma, g->sm_count, s));
+    CU(launch_multi_keys_out(keys, mg->d_counts + 2, mg->d_counts + 1, K, K, mg->d_item_seg, mg->d_lo, mg->d_perm,
+                             mg->d_out, mg->d_sims, grid, s));
+    return KNN_OK;
+}
+
+static void free_multi(knn_multi *mg) {
+    if (!mg) return;
+    if (mg->exec) cudaGraphExecDestroy(mg->exec);
+    if (mg->exec_stream) {
+        cudaStreamSynchronize(mg->exec_stream);
+        if (mg->g && mg->g->last_stream == mg->exec_stream) mg->g->last_stream = nullptr;
+        cudaStreamDestroy(mg->exec_stream);
+    }
+    if (mg->joined) cudaEventDestroy(mg->joined);
+    for (void *p : {(void *)mg->h_meta, (void *)mg->h_vecs, (void *)mg->h_out, (void *)mg->h_sims})
+        if (p) cudaFreeHost(p);
+    for (void *p : {(void *)mg->d_meta, (void *)mg->d_vecs, (void *)mg->d_out, (void *)mg->d_sims})
+        if (p) cudaFree(p);
+    if (mg->g) free_graph(mg->g);
+    delete mg;
+}
+
+extern "C" {
+
+KNN_API knn_status knn_multi_create(const knn_params *params, int32_t graphs, const int64_t *n_init,
+                                    const int64_t *capacity, const float *init_vecs, int32_t use_graph,
+                                    void *stream, knn_multi **out) {
+    if (!params || !n_init || !capacity || !init_vecs || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (graphs < 1 || graphs > 65536) return fail(KNN_ERR_INVALID_ARG, "graphs %d outside 1..65536", graphs);
+    int64_t total = 0, init_total = 0;
+    for (int i = 0; i < graphs; ++i) {
+        if (n_init[i] < params->k + 1 || capacity[i] < n_init[i])
+            return fail(KNN_ERR_INVALID_ARG, "graph %d: need k+1 <= n_init <= capacity", i);
+        total += capacity[i];
+        init_total += n_init[i];
+    }
+    if (total >= (int64_t)INT32_MAX) return fail(KNN_ERR_CAPACITY, "capacities add up past 2^31");
+    knn_params p = *params;
+    p.capacity = total;
+    TRY(validate_params(p, p.k + 1));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    knn_multi *mg = new knn_multi();
+    mg->G = graphs;
+    mg->use_graph = use_graph != 0;
+    mg->M = p.max_batch;
+    knn_status st = graph_alloc(p, s, &mg->g);
+    if (st != KNN_OK) {
+        delete mg;
+        return st;
+    }
+    knn_graph *g = mg->g;
+    g->n = total;  // every slot is addressable; each graph's size is its own
+    auto build = [&]() -> knn_status {
+        // step tables: counts[4] | item_seg[M] | lo[G] | n[G] | first[G+1] | perm[M] | streams[M]
+        const size_t M = (size_t)mg->M, Gs = (size_t)graphs;
+        mg->meta_bytes = align_up(16, 16) + align_up(M * 4, 16) + 2 * align_up(Gs * 4, 16) +
+                         align_up((Gs + 1) * 4, 16) + align_up(M * 4, 16) + align_up(M * 8, 16);
+        CU(cudaMallocHost(&mg->h_meta, mg->meta_bytes));
+        CU(cudaMalloc(&mg->d_meta, mg->meta_bytes));
+        size_t off = 0;
+        auto carve = [&](size_t bytes) {
+            uint8_t *q = mg->d_meta + off;
+            off += align_up(bytes, 16);
+            return q;
+        };
+        mg->d_counts = (int32_t *)carve(16);
+        mg->d_item_seg = (int32_t *)carve(M * 4);
+        mg->d_lo = (uint32_t *)carve(Gs * 4);
+        mg->d_n = (uint32_t *)carve(Gs * 4);
+        mg->d_first = (int32_t *)carve((Gs + 1) * 4);
+        mg->d_perm = (int32_t *)carve(M * 4);
+        mg->d_streams = (uint64_t *)carve(M * 8);
+        CU(cudaMallocHost(&mg->h_vecs, M * p.dim * 4));
+        CU(cudaMalloc(&mg->d_vecs, M * p.dim * 4));
+        CU(cudaMallocHost(&mg->h_out, M * p.k * 8));
+        CU(cudaMalloc(&mg->d_out, M * p.k * 8));
+        CU(cudaMallocHost(&mg->h_sims, M * p.k * 4));
+        CU(cudaMalloc(&mg->d_sims, M * p.k * 4));
+        if (mg->use_graph) {
+            CU(cudaStreamCreateWithFlags(&mg->exec_stream, cudaStreamNonBlocking));
+            CU(cudaEventCreateWithFlags(&mg->joined, cudaEventDisableTiming));
+        }
+        // the graphs, one after another, each with its exact initial graph
+        int64_t base = 0, row = 0;
+        for (int i = 0; i < graphs; ++i) {
+            mg->lo.push_back((uint32_t)base);
+            mg->cap.push_back((uint32_t)capacity[i]);
+            mg->n.push_back(n_init[i]);
+            mg->cap_max = std::max(mg->cap_max, (uint32_t)capacity[i]);
+            TRY(append_rows(g, init_vecs + row * p.dim, n_init[i], base, g->X, true, s));
+            ExactArgs ea{};
+            ea.X = g->X + base * g->dp;
+            ea.out_ids = g->nbr_ids + base * p.k;
+            ea.out_d2 = g->nbr_d2 + base * p.k;
+            ea.n = n_init[i];
+            ea.k = p.k;
+            TRY(run_exact(g->dp, ea, s, &g->launches));
+            CU(launch_shift_ids(g->nbr_ids + base * p.k, n_init[i] * p.k, (int32_t)base, s));
+            base += capacity[i];
+            row += n_init[i];
+        }
+        CU(cudaStreamSynchronize(s));
+        return KNN_OK;
+    };
+    st = build();
+    if (st != KNN_OK) {
+        free_multi(mg);
+        return st;
+    }
+    (void)init_total;
+    *out = mg;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_multi_step(knn_multi *mg, const float *vecs, const int32_t *graph, const int32_t *kind,
+                                  const uint64_t *query_ids, int64_t m, int64_t *out_ids, float *out_sims,
+                                  void *stream) {
+    if (!mg || !vecs || !graph || !kind || !out_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (m < 1 || m > mg->M) return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
+    knn_graph *g = mg->g;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mg->use_graph) {
+        // work on the graph's own stream, after what the caller's stream has queued
+        CU(cudaEventRecord(mg->joined, s));
+        CU(cudaStreamWaitEvent(mg->exec_stream, mg->joined, 0));
+        s = mg->exec_stream;
+    }
+    g->last_stream = s;
+    const int G = mg->G, d = g->p.dim, K = g->p.k;
+    // order: inserts grouped by graph (in given order), then queries
+    std::vector<int64_t> ins_count((size_t)G, 0);
+    int64_t m_ins = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (graph[i] < 0 || graph[i] >= G) return fail(KNN_ERR_INVALID_ARG, "item %lld: bad graph", (long long)i);
+        if (kind[i] != KNN_REQ_INSERT && kind[i] != KNN_REQ_QUERY)
+            return fail(KNN_ERR_INVALID_ARG, "item %lld: bad kind", (long long)i);
+        if (kind[i] == KNN_REQ_INSERT) {
+            ++ins_count[(size_t)graph[i]];
+            ++m_ins;
+        } else if (!query_ids) {
+            return fail(KNN_ERR_INVALID_ARG, "query items need query_ids");
+        }
+    }
+    for (int i = 0; i < G; ++i)
+        if (mg->n[(size_t)i] + ins_count[(size_t)i] > mg->cap[(size_t)i])
+            return fail(KNN_ERR_CAPACITY, "graph %d full", i);
+    uint8_t *h = mg->h_meta;
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        uint8_t *q = h + off;
+        off += align_up(bytes, 16);
+        return q;
+    };
+    const size_t M = (size_t)mg->M, Gs = (size_t)G;
+    int32_t *counts = (int32_t *)carve(16);
+    int32_t *item_seg = (int32_t *)carve(M * 4);
+    uint32_t *lo = (uint32_t *)carve(Gs * 4);
+    uint32_t *nn = (uint32_t *)carve(Gs * 4);
+    int32_t *first = (int32_t *)carve((Gs + 1) * 4);
+    int32_t *perm = (int32_t *)carve(M * 4);
+    uint64_t *streams = (uint64_t *)carve(M * 8);
+    first[0] = 0;
+    for (int i = 0; i < G; ++i) {
+        lo[i] = mg->lo[(size_t)i];
+        nn[i] = (uint32_t)mg->n[(size_t)i];
+        first[i + 1] = first[i] + (int32_t)ins_count[(size_t)i];
+    }
+    std::vector<int32_t> cursor(first, first + G);
+    int32_t qpos = (int32_t)m_ins;
+    for (int64_t i = 0; i < m; ++i) {
+        int32_t slot;
+        if (kind[i] == KNN_REQ_INSERT) {
+            const int gi = graph[i];
+            slot = cursor[(size_t)gi]++;
+            streams[slot] = mg->n[(size_t)gi] + (uint64_t)(slot - first[gi]);  // the new node's local id
+        } else {
+            slot = qpos++;
+            streams[slot] = (1ull << 63) + query_ids[i];
+        }
+        item_seg[slot] = graph[i];
+        perm[slot] = (int32_t)i;
+        std::memcpy(mg->h_vecs + (size_t)slot * d, vecs + i * d, (size_t)d * 4);
+    }
+    counts[0] = (int32_t)m;
+    counts[1] = (int32_t)m_ins;
+    counts[2] = (int32_t)(m - m_ins);
+    counts[3] = 0;
+    CU(cudaMemcpyAsync(mg->d_meta, mg->h_meta, mg->meta_bytes, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(mg->d_vecs, mg->h_vecs, (size_t)m * d * 4, cudaMemcpyHostToDevice, s));
+    if (mg->use_graph && mg->steps >= 1) {
+        if (!mg->exec) {
+            // capture the launch sequence once (the first step ran it directly)
+            cudaGraph_t graph_obj = nullptr;
+            CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const knn_status st = multi_launch(mg, s);
+            const cudaError_t ec = cudaStreamEndCapture(s, &graph_obj);
+            if (st != KNN_OK) return st;
+            CU(ec);
+            const cudaError_t ei = cudaGraphInstantiate(&mg->exec, graph_obj, 0);
+            cudaGraphDestroy(graph_obj);
+            CU(ei);
+        }
+        CU(cudaGraphLaunch(mg->exec, s));
+        g->launches += 1;
+    } else {
+        TRY(multi_launch(mg, s));
+        g->launches += 9;
+    }
+    CU(cudaMemcpyAsync(mg->h_out, mg->d_out, (size_t)m * K * 8, cudaMemcpyDeviceToHost, s));
+    if (out_sims) CU(cudaMemcpyAsync(mg->h_sims, mg->d_sims, (size_t)m * K * 4, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < m; ++i) {
+        if (kind[i] == KNN_REQ_QUERY) {
+            std::memcpy(out_ids + i * K, mg->h_out + i * K, (size_t)K * 8);
+            if (out_sims) std::memcpy(out_sims + i * K, mg->h_sims + i * K, (size_t)K * 4);
+        }
+    }
+    for (int i = 0; i < G; ++i) {
+        for (int32_t slot = first[i]; slot < first[i + 1]; ++slot) {
+            const int64_t orig = perm[slot];
+            out_ids[orig * K] = mg->n[(size_t)i] + (slot - first[i]);
+            for (int c = 1; c < K; ++c) out_ids[orig * K + c] = -1;
+            if (out_sims)
+                for (int c = 0; c < K; ++c) out_sims[orig * K + c] = 0.f;
+        }
+        mg->n[(size_t)i] += ins_count[(size_t)i];
+    }
+    g->inserts += m_ins;
+    g->queries += m - m_ins;
+    g->last_m = m;
+    ++mg->steps;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_multi_set_launch(knn_multi *mg, int32_t search_warps) {
+    if (!mg || search_warps < 0) return fail(KNN_ERR_INVALID_ARG, "bad argument");
+    if (search_warps != mg->search_warps && mg->exec) {
+        cudaStreamSynchronize(mg->exec_stream);
+        cudaGraphExecDestroy(mg->exec);  // captured with the old launch: capture again
+        mg->exec = nullptr;
+    }
+    mg->search_warps = search_warps;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_multi_graph_size(knn_multi *mg, int32_t graph, int64_t *n, int64_t *capacity) {
+    if (!mg || graph < 0 || graph >= mg->G) return fail(KNN_ERR_INVALID_ARG, "bad graph");
+    if (n) *n = mg->n[(size_t)graph];
+    if (capacity) *capacity = mg->cap[(size_t)graph];
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_multi_get_edges(knn_multi *mg, int32_t graph, int64_t *out_ids, void *stream) {
+    if (!mg || !out_ids || graph < 0 || graph >= mg->G) return fail(KNN_ERR_INVALID_ARG, "bad argument");
+    knn_graph *g = mg->g;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int K = g->p.k;
+    const int64_t n = mg->n[(size_t)graph], base = mg->lo[(size_t)graph];
+    std::vector<int32_t> ids((size_t)(n * K));
+    CU(cudaMemcpyAsync(ids.data(), g->nbr_ids + base * K, ids.size() * 4, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    std::vector<int64_t> local(ids.size());
+    for (size_t i = 0; i < ids.size(); ++i) local[i] = ids[i] < 0 ? -1 : (int64_t)ids[i] - base;
+    CU(cudaMemcpyAsync(out_ids, local.data(), local.size() * 8, cudaMemcpyDefault, s));
+    CU(cudaStreamSynchronize(s));
+    return KNN_OK;
+}
+
+KNN_API void knn_multi_destroy(knn_multi *mg) {
+    if (!mg) return;
+    DeviceGuard dg(mg->g->device);
+    cudaStreamSynchronize(mg->g->last_stream);
+    free_multi(mg);
+}
+
+}  // extern "C"

@@ -40,6 +40,25 @@ enum ErrorFlag : unsigned {
     ERR_OFFER_OVERFLOW = 1u,
 };
 
+// Several graphs in one node arena (knn_multi_*).  Graph s owns the nodes
+// lo[s] .. lo[s] + capacity - 1 and has n[s] nodes before a step; the
+// step's new points of graph s are insert items first[s] .. first[s+1] - 1
+// and take the ids lo[s] + n[s] + (item - first[s]).  A launch given an
+// item_seg table reads its item count from *count and loops over its items
+// with a fixed grid, so that one captured sequence of launches serves any
+// step.
+struct Segments {
+    const int32_t *item_seg = nullptr;   // [items] graph of each item (nullptr: one graph)
+    const uint32_t *lo = nullptr;        // [S] first node of each graph
+    const uint32_t *n = nullptr;         // [S] nodes before the step
+    const int32_t *first = nullptr;      // [S + 1] insert items of each graph
+    const int32_t *count = nullptr;      // device item count of the launch
+};
+
+__host__ __device__ __forceinline__ uint32_t seg_new_id(const Segments &sg, int32_t s, int32_t item) {
+    return sg.lo[s] + sg.n[s] + (uint32_t)(item - sg.first[s]);
+}
+
 struct SearchArgs {
     const uint8_t *rows;         // searched copy, row stride = row bytes of the encoding
     const float *row_scale;      // FP8: per-row scale
@@ -73,6 +92,7 @@ struct SearchArgs {
     double speedup = 1.0;
     uint32_t vis_n = 0;                  // bits of one visited set (n, or the largest partition)
     const uint64_t *streams = nullptr;   // nullable: restart stream of query i (replaces stream_base + i)
+    Segments seg;                        // several graphs: item i searches graph seg.item_seg[i]
 };
 constexpr uint64_t PART_STREAM_STEP = 1ull << 56;
 
@@ -84,6 +104,7 @@ struct RescoreArgs {
     uint64_t *out_keys;          // [m][k_out]
     unsigned long long *totals;
     int32_t m, KT, k_out;
+    const int32_t *m_dev = nullptr;      // nullable: device item count (fixed grid, loop)
 };
 
 struct CrossArgs {
@@ -94,6 +115,7 @@ struct CrossArgs {
     unsigned long long *totals;
     int32_t m, k;
     uint32_t n;
+    Segments seg;                        // several graphs: only points of one graph meet
 };
 
 struct UpdateArgs {
@@ -117,6 +139,7 @@ struct UpdateArgs {
     int64_t seen_words;          // ceil((n + m) / 32)
     int32_t m, k, depth;
     uint32_t n;                  // graph size before the batch
+    Segments seg;                // several graphs: seen bits relative to the graph's first node
 };
 
 struct MergeArgs {
@@ -179,6 +202,17 @@ cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned 
 // snapshot restore: copy int64 lists (checking every id) and recompute their d2
 cudaError_t launch_restore_lists(int dp, const float *rows, const int64_t *in_ids, int64_t n, int k,
                                  int32_t *nbr_ids, float *nbr_d2, unsigned *bad, cudaStream_t s);
+
+// several graphs in one arena (misc.cu): staged vectors to query rows and,
+// for insert items, to their new nodes; query keys to outputs in caller
+// order with graph-local ids; shifting an exact graph's local ids
+cudaError_t launch_multi_append(const float *in, const int32_t *count_all, const Segments &ins, int d, int dp,
+                                float *q_rows, float *rows, uint16_t *rows_bf16, uint8_t *rows_fp8, float *scale,
+                                int grid, cudaStream_t s);
+cudaError_t launch_multi_keys_out(const uint64_t *keys, const int32_t *count_q, const int32_t *count_ins, int kk,
+                                  int k_out, const int32_t *item_seg, const uint32_t *lo, const int32_t *perm,
+                                  int64_t *out_ids, float *out_sims, int grid, cudaStream_t s);
+cudaError_t launch_shift_ids(int32_t *ids, int64_t count, int32_t add, cudaStream_t s);
 
 // p[i] += v for i < m (misc.cu)
 cudaError_t launch_add_u64(uint64_t *p, uint64_t v, int64_t m, cudaStream_t s);

@@ -38,17 +38,16 @@ cudaError_t launch_search(int storage, int dp, const SearchArgs &a, cudaStream_t
 // when asked, the BF16 copy (round to nearest even) or the FP8-E4M3 copy with
 // a per-row scale amax / 448 (code = e4m3(x / scale), round to nearest even,
 // saturating; a zero row gets scale 1).
-__global__ void append_kernel(const float *in, int64_t m, int d, int dp, float *rows,
-                              uint16_t *rows_bf16, uint8_t *rows_fp8, float *scale) {
+// One warp: row `x` (d floats) to row r of the stored copies.
+__device__ __forceinline__ void encode_row(const float *x, int d, int dp, int64_t r, float *rows,
+                                           uint16_t *rows_bf16, uint8_t *rows_fp8, float *scale) {
     const int lane = threadIdx.x & 31;
-    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (r >= m) return;
     float amax = 0.f;
     for (int c = lane; c < dp; c += 32) {
-        const float x = c < d ? in[r * d + c] : 0.f;
-        rows[r * dp + c] = x;
-        amax = fmaxf(amax, fabsf(x));
-        if (rows_bf16) rows_bf16[r * dp + c] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+        const float v = c < d ? x[c] : 0.f;
+        rows[r * dp + c] = v;
+        amax = fmaxf(amax, fabsf(v));
+        if (rows_bf16) rows_bf16[r * dp + c] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
     }
     if (rows_fp8) {
 #pragma unroll
@@ -56,10 +55,78 @@ __global__ void append_kernel(const float *in, int64_t m, int d, int dp, float *
         const float sc = amax > 0.f ? __fdiv_rn(amax, 448.0f) : 1.0f;
         if (lane == 0) scale[r] = sc;
         for (int c = lane; c < dp; c += 32) {
-            const float x = c < d ? in[r * d + c] : 0.f;
-            rows_fp8[r * dp + c] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(x, sc), __NV_SATFINITE, __NV_E4M3);
+            const float v = c < d ? x[c] : 0.f;
+            rows_fp8[r * dp + c] = (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(v, sc), __NV_SATFINITE, __NV_E4M3);
         }
     }
+}
+
+__global__ void append_kernel(const float *in, int64_t m, int d, int dp, float *rows,
+                              uint16_t *rows_bf16, uint8_t *rows_fp8, float *scale) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= m) return;
+    encode_row(in + r * d, d, dp, r, rows, rows_bf16, rows_fp8, scale);
+}
+
+// A step over several graphs: item i of the staged vectors (inserts first)
+// becomes query row i; an insert item is also stored at its new node.
+__global__ void multi_append_kernel(const float *in, const int32_t *count_all, Segments ins, int d, int dp,
+                                    float *q_rows, float *rows, uint16_t *rows_bf16, uint8_t *rows_fp8,
+                                    float *scale) {
+    const int m_all = *count_all, m_ins = *ins.count;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m_all; i += nw) {
+        encode_row(in + i * d, d, dp, i, q_rows, nullptr, nullptr, nullptr);
+        if (i < m_ins) {
+            const uint32_t node = seg_new_id(ins, ins.item_seg[i], (int32_t)i);
+            encode_row(in + i * d, d, dp, node, rows, rows_bf16, rows_fp8, scale);
+        }
+    }
+}
+
+cudaError_t launch_multi_append(const float *in, const int32_t *count_all, const Segments &ins, int d, int dp,
+                                float *q_rows, float *rows, uint16_t *rows_bf16, uint8_t *rows_fp8, float *scale,
+                                int grid, cudaStream_t s) {
+    multi_append_kernel<<<grid, 256, 0, s>>>(in, count_all, ins, d, dp, q_rows, rows, rows_bf16, rows_fp8, scale);
+    return cudaGetLastError();
+}
+
+// Query results of a step over several graphs: the m_q query items follow
+// the m_ins insert items; item i's k_out best keys go to output row perm[i]
+// with ids local to its graph.
+__global__ void multi_keys_out_kernel(const uint64_t *keys, const int32_t *count_q, const int32_t *count_ins,
+                                      int kk, int k_out, const int32_t *item_seg, const uint32_t *lo,
+                                      const int32_t *perm, int64_t *out_ids, float *out_sims) {
+    const int m_q = *count_q, m_ins = *count_ins;
+    const int64_t total = (int64_t)m_q * k_out;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / k_out), c = (int)(t % k_out);
+        const int i = m_ins + j;
+        const uint64_t key = keys[(size_t)i * kk + c];
+        const int64_t o = (int64_t)perm[i] * k_out + c;
+        out_ids[o] = key == KEY_EMPTY ? -1 : (int64_t)key_id(key) - (int64_t)lo[item_seg[i]];
+        if (out_sims) out_sims[o] = key == KEY_EMPTY ? 0.f : sim_of_d2(key_d2(key));
+    }
+}
+
+cudaError_t launch_multi_keys_out(const uint64_t *keys, const int32_t *count_q, const int32_t *count_ins, int kk,
+                                  int k_out, const int32_t *item_seg, const uint32_t *lo, const int32_t *perm,
+                                  int64_t *out_ids, float *out_sims, int grid, cudaStream_t s) {
+    multi_keys_out_kernel<<<grid, 256, 0, s>>>(keys, count_q, count_ins, kk, k_out, item_seg, lo, perm, out_ids,
+                                               out_sims);
+    return cudaGetLastError();
+}
+
+// ids[i] += add for the i < count entries that are >= 0
+__global__ void shift_ids_kernel(int32_t *ids, int64_t count, int32_t add) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count && ids[t] >= 0) ids[t] += add;
+}
+
+cudaError_t launch_shift_ids(int32_t *ids, int64_t count, int32_t add, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    shift_ids_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ids, count, add);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_append(const float *in, int64_t m, int d, int dp, float *rows_fp32,

@@ -114,21 +114,32 @@ ignns_search_kernel(const SearchArgs a) {
     const RowSource src{a.rows, a.row_scale};
     const int nwarps = gridDim.x * SEARCH_WARPS;
     const float INF = __int_as_float(0x7f800000);
-    const int nsearch = a.m * a.parts;
+    const bool multi = a.seg.item_seg != nullptr;
+    const int nsearch = multi ? *a.seg.count : a.m * a.parts;
 
     // search sw: query sw / parts over partition sw % parts, the nodes
-    // lo .. lo + np - 1 (one partition: every node)
+    // lo .. lo + np - 1 (one partition: every node); with several graphs,
+    // item sw over its graph's nodes
     for (int sw = blockIdx.x * SEARCH_WARPS + wib; sw < nsearch; sw += nwarps) {
-        const int qi = sw / a.parts, part = sw % a.parts;
-        const uint32_t lo = a.parts > 1 ? (uint32_t)a.part_off[part] : 0u;
-        const uint32_t np = a.parts > 1 ? (uint32_t)(a.part_off[part + 1] - (int64_t)lo) : a.n;
-        const int64_t live = a.parts > 1 ? a.part_live[part] : a.n_live;
-        int64_t budget = a.budget;
-        if (a.parts > 1) {
+        const int qi = multi ? sw : sw / a.parts, part = multi ? 0 : sw % a.parts;
+        uint32_t lo = 0u, np = a.n;
+        int64_t live = a.n_live, budget = a.budget;
+        uint64_t max_draws = a.max_draws;
+        if (multi || a.parts > 1) {
+            if (multi) {
+                const int sg = a.seg.item_seg[sw];
+                lo = a.seg.lo[sg];
+                np = a.seg.n[sg];
+                live = np;
+            } else {
+                lo = (uint32_t)a.part_off[part];
+                np = (uint32_t)(a.part_off[part + 1] - (int64_t)lo);
+                live = a.part_live[part];
+            }
             const double b = floor((double)np / a.speedup);  // max(1, floor(n / speedup))
             budget = b < 1.0 ? 1 : (int64_t)b;
+            max_draws = 64ull * np;
         }
-        const uint64_t max_draws = a.parts > 1 ? 64ull * np : a.max_draws;
         // each evaluation visits a new node, so evals also counts visited nodes
         const int limit = (int)(budget < live ? budget : live);
         float qv[C::QF];

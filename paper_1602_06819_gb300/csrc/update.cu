@@ -36,11 +36,8 @@ constexpr int UPD_WARPS = 4;
 // FP32 re-score of screening candidates (best KT by screening distance).
 // ---------------------------------------------------------------------------
 template <int DP>
-__global__ void __launch_bounds__(UPD_WARPS * 32) rescore_kernel(const RescoreArgs a) {
+__device__ __forceinline__ void rescore_item(const RescoreArgs &a, int item, int lane) {
     using C = RowCfg<ST_FP32, DP>;
-    const int lane = threadIdx.x & 31;
-    const int item = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5);
-    if (item >= a.m) return;
     float qv[C::QF];
     load_query<ST_FP32, DP>(a.queries + (size_t)item * a.q_stride, qv);
     const RowSource src{reinterpret_cast<const uint8_t *>(a.rows), nullptr};
@@ -63,16 +60,30 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) rescore_kernel(const RescoreAr
     if (lane == 0) atomicAdd(a.totals + TOT_RESCORE_EVALS, (unsigned long long)n_scored);
 }
 
+template <int DP>
+__global__ void __launch_bounds__(UPD_WARPS * 32) rescore_kernel(const RescoreArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int m = a.m_dev ? *a.m_dev : a.m;
+    for (int item = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5); item < m; item += gridDim.x * UPD_WARPS)
+        rescore_item<DP>(a, item, lane);
+}
+
 // ---------------------------------------------------------------------------
 // Cross-merge among the points of one batch.
 // ---------------------------------------------------------------------------
 template <int DP>
-__global__ void __launch_bounds__(UPD_WARPS * 32) cross_kernel(const CrossArgs a) {
+__device__ __forceinline__ void cross_item(const CrossArgs &a, int i, int lane) {
     using C = RowCfg<ST_FP32, DP>;
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5);
-    if (i >= a.m) return;
-    const uint32_t new_id = a.n + (uint32_t)i;
+    // the new point's id and the batch points it meets: those of its graph
+    uint32_t id0 = a.n;
+    int j_lo = 0, j_hi = a.m;
+    if (a.seg.item_seg) {
+        const int sg = a.seg.item_seg[i];
+        j_lo = a.seg.first[sg];
+        j_hi = a.seg.first[sg + 1];
+        id0 = a.seg.lo[sg] + a.seg.n[sg];
+    }
+    const uint32_t new_id = id0 + (uint32_t)(i - j_lo);
     float qv[C::QF];
     load_query<ST_FP32, DP>(a.rows + (size_t)new_id * DP, qv);
     const RowSource src{reinterpret_cast<const uint8_t *>(a.rows), nullptr};
@@ -80,13 +91,13 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) cross_kernel(const CrossArgs a
     top.init(a.k);
     top.e[0] = lane < a.k ? a.in_keys[(size_t)i * a.k + lane] : KEY_EMPTY;
     top.worst = top.entry(a.k - 1);
-    for (int j0 = 0; j0 < a.m; j0 += 32) {
-        const int nr = a.m - j0 < 32 ? a.m - j0 : 32;
-        const uint32_t id = a.n + (uint32_t)(j0 + lane);
+    for (int j0 = j_lo; j0 < j_hi; j0 += 32) {
+        const int nr = j_hi - j0 < 32 ? j_hi - j0 : 32;
+        const uint32_t id = id0 + (uint32_t)(j0 - j_lo + lane);
         const float d2 = gather_d2<ST_FP32, DP>(src, id, nr, qv);
         for (int t = 0; t < nr; ++t) {
             if (j0 + t == i) continue;
-            top.offer(pack_key(__shfl_sync(FULL, d2, t), a.n + (uint32_t)(j0 + t)));
+            top.offer(pack_key(__shfl_sync(FULL, d2, t), id0 + (uint32_t)(j0 - j_lo + t)));
         }
     }
     if (lane < a.k) {
@@ -94,7 +105,15 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) cross_kernel(const CrossArgs a
         a.nbr_ids[(size_t)new_id * a.k + lane] = key == KEY_EMPTY ? -1 : (int32_t)key_id(key);
         a.nbr_d2[(size_t)new_id * a.k + lane] = key == KEY_EMPTY ? __int_as_float(0x7f800000) : key_d2(key);
     }
-    if (lane == 0 && a.m > 1) atomicAdd(a.totals + TOT_CROSS_EVALS, (unsigned long long)(a.m - 1));
+    if (lane == 0 && j_hi - j_lo > 1) atomicAdd(a.totals + TOT_CROSS_EVALS, (unsigned long long)(j_hi - j_lo - 1));
+}
+
+template <int DP>
+__global__ void __launch_bounds__(UPD_WARPS * 32) cross_kernel(const CrossArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int m = a.seg.count ? *a.seg.count : a.m;
+    for (int i = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5); i < m; i += gridDim.x * UPD_WARPS)
+        cross_item<DP>(a, i, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -134,16 +153,18 @@ __device__ __forceinline__ void push_offers(const UpdateArgs &a, bool has, uint3
 constexpr size_t UPD_SMEM_SEEN_MAX = 110 * 1024;
 
 template <int DP, bool SMEM_SEEN>
-__global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const UpdateArgs a) {
+__device__ __forceinline__ void offers_item(const UpdateArgs &a, int i, int lane, int wib, uint32_t *smem_seen) {
     using C = RowCfg<ST_FP32, DP>;
-    extern __shared__ uint32_t smem_seen[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int i = blockIdx.x * UPD_WARPS + wib;
-    if (i >= a.m) return;
-
-    const uint32_t new_id = a.n + (uint32_t)i;
+    // the new point, the end of its graph before the batch (nodes at or past
+    // it are points of this batch) and the first node of its graph
+    uint32_t new_id = a.n + (uint32_t)i, pre = a.n, base = 0u;
+    if (a.seg.item_seg) {
+        const int sg = a.seg.item_seg[i];
+        base = a.seg.lo[sg];
+        pre = base + a.seg.n[sg];
+        new_id = pre + (uint32_t)(i - a.seg.first[sg]);
+    }
     const RowSource src{reinterpret_cast<const uint8_t *>(a.rows), nullptr};
 
     // level 1: the new point's list (similarities known from the search)
@@ -152,7 +173,7 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const Upd
     {
         bool has = false;
         uint64_t key = 0;
-        if (lid >= 0 && (uint32_t)lid < a.n &&
+        if (lid >= 0 && (uint32_t)lid < pre &&
             !((__ldg(a.removed + (lid >> 5)) >> (lid & 31)) & 1u)) {
             key = pack_key(ld2, new_id);
             has = key < list_last_key(a, (uint32_t)lid);
@@ -172,8 +193,8 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const Upd
             seen = a.seen + (size_t)i * a.seen_words;
         }
         __syncwarp();
-        if (lane == 0) atomicOr(seen + (new_id >> 5), 1u << (new_id & 31));
-        if (lid >= 0) atomicOr(seen + ((uint32_t)lid >> 5), 1u << (lid & 31));
+        if (lane == 0) atomicOr(seen + ((new_id - base) >> 5), 1u << ((new_id - base) & 31));
+        if (lid >= 0) atomicOr(seen + (((uint32_t)lid - base) >> 5), 1u << (((uint32_t)lid - base) & 31));
         int32_t *level = a.frontier + (size_t)i * a.frontier_cap;  // the levels, one after another
         if (lane < a.k) level[lane] = lid;
         int lo = 0, hi = a.k;  // the current level is level[lo .. hi)
@@ -193,9 +214,10 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const Upd
                 if (u >= 0) w = __ldg(a.nbr_ids + (size_t)u * a.k + el);
                 bool keep = false;
                 if (w >= 0) {
-                    const uint32_t bit = 1u << (w & 31);
-                    const uint32_t old = atomicOr(seen + ((uint32_t)w >> 5), bit);
-                    keep = !(old & bit) && (uint32_t)w < a.n &&
+                    const uint32_t wl = (uint32_t)w - base;
+                    const uint32_t bit = 1u << (wl & 31);
+                    const uint32_t old = atomicOr(seen + (wl >> 5), bit);
+                    keep = !(old & bit) && (uint32_t)w < pre &&
                            !((__ldg(a.removed + (w >> 5)) >> (w & 31)) & 1u);
                 }
                 const unsigned km = __ballot_sync(FULL, keep);
@@ -229,6 +251,18 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const Upd
     if (lane == 0) {
         a.counters[(size_t)i * NCTR + CTR_UPDATE_EVALS] = upd_evals;
         atomicAdd(a.totals + TOT_UPDATE_EVALS, (unsigned long long)upd_evals);
+    }
+}
+
+template <int DP, bool SMEM_SEEN>
+__global__ void __launch_bounds__(UPD_WARPS * 32) update_offers_kernel(const UpdateArgs a) {
+    extern __shared__ uint32_t smem_seen[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int m = a.seg.count ? *a.seg.count : a.m;
+    for (int i = blockIdx.x * UPD_WARPS + wib; i < m; i += gridDim.x * UPD_WARPS) {
+        offers_item<DP, SMEM_SEEN>(a, i, lane, wib, smem_seen);
+        __syncwarp();
     }
 }
 

@@ -50,8 +50,10 @@ EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
             "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
             "knn_balanced_kmedoids", "knn_server_create", "knn_server_submit", "knn_server_wait",
-            "knn_server_get_stats", "knn_server_destroy", "knn_search_noalloc", "knn_last_error",
-            "knn_version")
+            "knn_server_get_stats", "knn_server_destroy", "knn_multi_create", "knn_multi_step",
+            "knn_multi_set_launch", "knn_multi_graph_size", "knn_multi_get_edges", "knn_multi_destroy",
+            "knn_search_noalloc",
+            "knn_last_error", "knn_version")
 
 KNN_REQ_INSERT = 0
 KNN_REQ_QUERY = 1
@@ -139,6 +141,12 @@ def _load_library() -> ctypes.CDLL:
         "knn_server_wait": (I32, [P, U64, P, P, ctypes.POINTER(KnnRequestInfo)]),
         "knn_server_get_stats": (I32, [P, ctypes.POINTER(KnnServerStats)]),
         "knn_server_destroy": (None, [P]),
+        "knn_multi_create": (I32, [ctypes.POINTER(KnnParams), I32, P, P, P, I32, P, ctypes.POINTER(P)]),
+        "knn_multi_step": (I32, [P, P, P, P, P, I64, P, P, P]),
+        "knn_multi_set_launch": (I32, [P, I32]),
+        "knn_multi_graph_size": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "knn_multi_get_edges": (I32, [P, I32, P, P]),
+        "knn_multi_destroy": (None, [P]),
         "knn_balanced_kmedoids": (I32, [P, I64, I32, I32, ctypes.c_double, I32, I32, U64, P, P, P, P, P]),
         "knn_graph_set_search": (I32, [P, ctypes.c_double, ctypes.c_double, I32]),
         "knn_exact_last_info": (I32, [ctypes.POINTER(KnnExactInfo)]),
@@ -482,6 +490,100 @@ class Server:
     def close(self):
         if self.handle:
             lib.knn_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class MultiGraph:
+    """Several graphs in one device arena, stepped with mixed batches
+    (knn_multi_*).  Host numpy arrays in, host numpy arrays out."""
+
+    def __init__(self, cfg: GraphConfig, n_init, capacity, init_vecs, use_graph: bool = True,
+                 stream=None):
+        self.cfg = cfg
+        n_init = np.ascontiguousarray(n_init, dtype=np.int64)
+        capacity = np.ascontiguousarray(capacity, dtype=np.int64)
+        _check_dtype(init_vecs, "float32", "init_vecs")
+        h = ctypes.c_void_p()
+        _check(lib.knn_multi_create(ctypes.byref(cfg.params()), n_init.shape[0], n_init.ctypes.data,
+                                    capacity.ctypes.data, _ptr(init_vecs), int(bool(use_graph)),
+                                    _stream(stream), ctypes.byref(h)), "knn_multi_create")
+        self.handle = h
+        self.graphs = n_init.shape[0]
+
+    def step(self, vecs, graph, kind, query_ids=None, with_sims: bool = False):
+        v = np.ascontiguousarray(vecs, dtype=np.float32)
+        gr = np.ascontiguousarray(graph, dtype=np.int32)
+        kd = np.ascontiguousarray(kind, dtype=np.int32)
+        m = v.shape[0]
+        qid = np.ascontiguousarray(np.zeros(m, np.uint64) if query_ids is None else query_ids, dtype=np.uint64)
+        out = np.empty((m, self.cfg.k), np.int64)
+        sims = np.empty((m, self.cfg.k), np.float32) if with_sims else None
+        _check(lib.knn_multi_step(self.handle, v.ctypes.data, gr.ctypes.data, kd.ctypes.data, qid.ctypes.data, m,
+                                  out.ctypes.data, None if sims is None else sims.ctypes.data, None),
+               "knn_multi_step")
+        return out, sims
+
+    def set_launch(self, search_warps: int):
+        _check(lib.knn_multi_set_launch(self.handle, search_warps), "knn_multi_set_launch")
+
+    def autotune(self, sample, step_caps=(512, 1024, 2048, 4096), warps=(608, 1216, 2432, 0),
+                 repeats: int = 2) -> dict:
+        """Pick the search launch width and the step size cap by timing
+        query-only steps of `sample` (vecs, graph, query_ids: read-only, so
+        the graphs do not change).  Returns the chosen settings and the times
+        measured; the chosen launch width is set, the step cap is returned for
+        the caller's batching (step_many)."""
+        import time
+        vecs, graph, qids = sample
+        kind = np.ones(len(graph), np.int32)
+        best, table = None, []
+        for w in warps:
+            self.set_launch(w)
+            for cap in step_caps:
+                if cap > self.cfg.max_batch:
+                    continue
+                self.step_many(vecs[:cap], graph[:cap], kind[:cap], qids[:cap], cap)  # warm (and capture)
+                t0 = time.perf_counter()
+                for _ in range(repeats):
+                    self.step_many(vecs, graph, kind, qids, cap)
+                dt = (time.perf_counter() - t0) / repeats
+                rate = len(graph) / dt
+                table.append({"search_warps": w, "step_cap": cap, "items_per_s": rate})
+                if best is None or rate > best["items_per_s"]:
+                    best = table[-1]
+        self.set_launch(best["search_warps"])
+        return {"best": best, "tried": table}
+
+    def step_many(self, vecs, graph, kind, query_ids, cap: int):
+        """Items in steps of at most `cap`, in order; the concatenated outputs."""
+        outs = []
+        for i in range(0, len(graph), cap):
+            o, _ = self.step(vecs[i:i + cap], graph[i:i + cap], kind[i:i + cap],
+                             None if query_ids is None else query_ids[i:i + cap])
+            outs.append(o)
+        return np.concatenate(outs)
+
+    def size(self, graph: int):
+        n, c = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.knn_multi_graph_size(self.handle, graph, ctypes.byref(n), ctypes.byref(c)),
+               "knn_multi_graph_size")
+        return n.value, c.value
+
+    def edges(self, graph: int) -> np.ndarray:
+        n, _ = self.size(graph)
+        out = np.empty((n, self.cfg.k), np.int64)
+        _check(lib.knn_multi_get_edges(self.handle, graph, out.ctypes.data, None), "knn_multi_get_edges")
+        return out
+
+    def close(self):
+        if self.handle:
+            lib.knn_multi_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):
