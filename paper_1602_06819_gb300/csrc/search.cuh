@@ -115,6 +115,10 @@ ignns_search_kernel(const SearchArgs a) {
     const int nwarps = gridDim.x * SEARCH_WARPS;
     const float INF = __int_as_float(0x7f800000);
     const bool multi = a.seg.item_seg != nullptr;
+    // climb list prefetch: lane l holds entry pf_p of the list of neighbour
+    // pf_j, for the first npf = floor(32 / k) neighbours
+    const int npf = 32 / a.k;
+    const int pf_j = lane / a.k < npf ? lane / a.k : 0, pf_p = lane % a.k;
     const int nsearch = multi ? *a.seg.count : a.m * a.parts;
 
     // search sw: query sw / parts over partition sw % parts, the nodes
@@ -261,13 +265,18 @@ ignns_search_kernel(const SearchArgs a) {
                 // ---- eager hill climbing from the kept restart
                 uint32_t cur = __shfl_sync(FULL, aid, ai);
                 float d2cur = d2a;
+                int32_t nb = lane < a.k ? (int32_t)ld_nc_u32(a.nbr + (size_t)cur * a.k + lane) : -1;
                 while (true) {
-                    const int32_t nb = lane < a.k ? (int32_t)ld_nc_u32(a.nbr + (size_t)cur * a.k + lane) : -1;
                     ++adj;
                     // a partition follows only its own nodes (Algorithm 3)
                     const bool valid = nb >= 0 && (uint32_t)nb - lo < np && !test_bit_ro(a.removed, (uint32_t)nb);
                     __syncwarp();
                     const bool seen = valid && vis.test((uint32_t)nb);
+                    // the lists of the first 32 / k neighbours load in the same
+                    // round trip as their rows (lane l: entry pf_p of neighbour
+                    // pf_j), so a move to one of them needs no list load
+                    const int32_t nbj = __shfl_sync(FULL, nb, pf_j);
+                    const int32_t pfl = (pf_j < npf && nbj >= 0) ? (int32_t)ld_nc_u32(a.nbr + (size_t)nbj * a.k + pf_p) : -1;
                     const float nd2 = gather_d2<STORAGE, DP>(src, valid ? (uint32_t)nb : 0u, a.k, qv);
                     unsigned um = __ballot_sync(FULL, valid && !seen);
                     if (um == 0u) break;  // every neighbour visited: local maximum
@@ -306,6 +315,12 @@ ignns_search_kernel(const SearchArgs a) {
                     if (mi == 32) break;  // no unvisited neighbour is more similar
                     cur = (uint32_t)__shfl_sync(FULL, nb, mi);  // first strict increase: move
                     d2cur = __shfl_sync(FULL, nd2, mi);
+                    if (mi < npf) {  // its list came with the rows
+                        const int32_t v = __shfl_sync(FULL, pfl, (mi * a.k + lane) & 31);
+                        nb = lane < a.k ? v : -1;
+                    } else {
+                        nb = lane < a.k ? (int32_t)ld_nc_u32(a.nbr + (size_t)cur * a.k + lane) : -1;
+                    }
                 }
                 if (done) break;
                 // the climb may have visited candidates drawn earlier
