@@ -305,6 +305,17 @@ typedef struct knn_exact_info {
 KNN_API knn_status knn_exact_last_info(knn_exact_info *out);
 
 /*
+ * Failure detection of the tensor-core build: every wait of one of its
+ * pipeline roles on another gives up after `ns` nanoseconds (default 2 s;
+ * ns < 0 restores it), records the wait in knn_exact_info.wait_errors and
+ * sends the rows of that block to the FP32 pass, which keeps the lists
+ * exact.  A block always waits for its own copies and MMAs before it exits.
+ * Process-wide; meant for tests (ns = 0 makes every pipeline wait that is
+ * not already satisfied give up).
+ */
+KNN_API knn_status knn_exact_set_wait_limit(int64_t ns);
+
+/*
  * The query search of knn_graph_query_batch (FP32 rows, no removed nodes)
  * over a graph held in the caller's own device buffers, without any device
  * allocation.  The paper has no counterpart: this exists for callers that

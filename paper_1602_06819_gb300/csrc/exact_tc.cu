@@ -31,9 +31,11 @@
 // kernel.  The lists therefore equal the exact ones up to FP32 rounding of
 // the distances.
 //
-// Every mbarrier wait is bounded.  A wait that gives up sets a bit of the
-// error word, and the rows of that CTA are marked for the FP32 pass, so the
-// result stays exact.
+// Every mbarrier wait is bounded.  A pipeline wait (one role waiting for
+// another) that gives up after wait_ns sets a bit of the error word and the
+// rows of that CTA are marked for the FP32 pass, so the result stays exact;
+// before the CTA exits, every copy and MMA it issued is waited for (drain
+// waits, on work that completes by itself) so that nothing is left in flight.
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -53,7 +55,7 @@ constexpr int TC_EPI = 256;             // epilogue threads
 constexpr int TC_BUF = 32;              // buffered keys per epilogue thread
 constexpr uint32_t TC_BOX = 128 * 128;  // bytes of one 128-row x 64-element BF16 box
 constexpr uint32_t TC_UNIT = 2 * TC_BOX;  // hi and lo boxes of one K slice
-constexpr uint64_t TC_WAIT = 2000000000ull;  // ns before a wait gives up
+constexpr uint64_t TC_WAIT = 2000000000ull;  // ns before a drain wait gives up (the default pipeline limit too)
 
 // NBOX 64-element K slices per row (padded width 64 * NBOX)
 template <int NBOX>
@@ -115,7 +117,7 @@ template <int NBOX>
 __global__ void __launch_bounds__(384, 1)
 exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant__ CUtensorMap t_lo,
                 const float *__restrict__ norm2, int64_t n, int32_t *cand_id, float *cand_key,
-                unsigned *err) {
+                unsigned *err, uint64_t wait_ns) {
     using Cfg = TcCfg<NBOX>;
     constexpr int S = Cfg::STAGES;
     extern __shared__ uint8_t tc_raw[];
@@ -170,7 +172,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         int issued = 0;
         for (int u = 0; u < units; ++u) {
             const int s = u % S;
-            if (u >= S && !mbar_wait(b_empty + s, ((u / S) - 1) & 1, TC_WAIT)) {
+            if (u >= S && !mbar_wait(b_empty + s, ((u / S) - 1) & 1, wait_ns)) {
                 atomicOr(err, 1u);
                 break;
             }
@@ -189,18 +191,18 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer: acc = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
         constexpr uint32_t idesc = idesc_bf16_f32(TC_ROWS, TC_COLS);
-        bool ok = mbar_wait(a_full, 0, TC_WAIT);
+        bool ok = mbar_wait(a_full, 0, wait_ns);
         if (!ok) atomicOr(err, 2u);
         for (int t = 0; ok && t < ntiles; ++t) {
             const int buf = t & 1;
-            if (t >= 2 && !mbar_wait(acc_empty + buf, ((t / 2) - 1) & 1, TC_WAIT)) {
+            if (t >= 2 && !mbar_wait(acc_empty + buf, ((t / 2) - 1) & 1, wait_ns)) {
                 atomicOr(err, 8u);
                 break;
             }
             const uint32_t d = tmem + buf * TC_COLS;
             for (int kb = 0; kb < NBOX; ++kb) {
                 const int u = t * NBOX + kb, s = u % S;
-                if (!mbar_wait(b_full + s, (u / S) & 1, TC_WAIT)) {
+                if (!mbar_wait(b_full + s, (u / S) & 1, wait_ns)) {
                     atomicOr(err, 4u);
                     ok = false;
                     break;
@@ -228,7 +230,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         int issued = 0;
         for (int t = 0; t < ntiles; ++t) {
             const int buf = t & 1;
-            if (t >= 2 && !mbar_wait(acc_empty + buf, ((t / 2) - 1) & 1, TC_WAIT)) {
+            if (t >= 2 && !mbar_wait(acc_empty + buf, ((t / 2) - 1) & 1, wait_ns)) {
                 atomicOr(err, 128u);
                 break;
             }
@@ -275,8 +277,8 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
             const int buf = t & 1;
             const int64_t c_base = (int64_t)t * TC_COLS;
             if (ok)
-                ok = __all_sync(FULL, mbar_wait(acc_full + buf, (t / 2) & 1, TC_WAIT) &&
-                                          mbar_wait(yn_full + buf, (t / 2) & 1, TC_WAIT));
+                ok = __all_sync(FULL, mbar_wait(acc_full + buf, (t / 2) & 1, wait_ns) &&
+                                          mbar_wait(yn_full + buf, (t / 2) & 1, wait_ns));
             if (!ok && lane == 0) atomicOr(err, 16u);
             fence_after_sync();
             if (ok) {
@@ -466,6 +468,10 @@ size_t exact_tc_scratch_bytes(int64_t n, int dp) {
            align256((size_t)n * 4) + 256 + align256((size_t)EXACT_PARTIAL_SLOTS * 32 * 8);
 }
 
+static uint64_t g_tc_wait_ns = TC_WAIT;
+
+void exact_tc_set_wait(int64_t ns) { g_tc_wait_ns = ns < 0 ? TC_WAIT : (uint64_t)ns; }
+
 template <int NBOX>
 static cudaError_t tc_screen(const CUtensorMap &th, const CUtensorMap &tl, const float *norm2, int64_t n,
                              int32_t *cid, float *ckey, unsigned *err, cudaStream_t s) {
@@ -474,7 +480,7 @@ static cudaError_t tc_screen(const CUtensorMap &th, const CUtensorMap &tl, const
         cudaFuncSetAttribute(exact_tc_kernel<NBOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     exact_tc_kernel<NBOX><<<(unsigned)((n + TC_ROWS - 1) / TC_ROWS), 384, smem, s>>>(th, tl, norm2, n, cid, ckey,
-                                                                                     err);
+                                                                                     err, g_tc_wait_ns);
     return cudaGetLastError();
 }
 

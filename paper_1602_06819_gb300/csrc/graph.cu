@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "knn_graph.h"
 #include "common.cuh"
 #include "kernels.h"
@@ -127,6 +129,12 @@ knn_status knn::record_error(knn_status st, const char *msg) {
             return fail(KNN_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                 \
                         cudaGetErrorString(e_), __FILE__, __LINE__);                  \
     } while (0)
+
+// An NVTX range around an ABI call (visible in Nsight tools; free otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct DeviceGuard {
     int prev = -1;
@@ -476,6 +484,7 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
 
 KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_vecs, int64_t n_init,
                                     void *stream, knn_graph **out) {
+    NvtxRange nvtx_range("knn_graph_create");
     if (!params || !init_vecs || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     TRY(validate_params(*params, n_init));
@@ -507,6 +516,7 @@ KNN_API knn_status knn_graph_create(const knn_params *params, const float *init_
 
 KNN_API knn_status knn_graph_restore(const knn_params *params, const float *vecs, int64_t n,
                                      const int64_t *nbr_ids, void *stream, knn_graph **out) {
+    NvtxRange nvtx_range("knn_graph_restore");
     if (!params || !vecs || !nbr_ids || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     TRY(validate_params(*params, n));
@@ -544,6 +554,7 @@ KNN_API knn_status knn_graph_restore(const knn_params *params, const float *vecs
 
 KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64_t m, int64_t *out_ids,
                                           int64_t *out_nbrs, void *stream) {
+    NvtxRange nvtx_range("knn_graph_insert_batch");
     if (!g || !vecs) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 1 || m > g->p.max_batch)
         return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
@@ -653,6 +664,7 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
 KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
                                          uint64_t query_id0, int64_t *out_ids, float *out_sims,
                                          void *stream) {
+    NvtxRange nvtx_range("knn_graph_query_batch");
     if (!g || !vecs || !out_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 1 || m > g->p.max_batch)
         return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
@@ -679,6 +691,7 @@ KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_
 KNN_API knn_status knn_graph_query_ids(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
                                        const uint64_t *query_ids, int64_t *out_ids, float *out_sims,
                                        void *stream) {
+    NvtxRange nvtx_range("knn_graph_query_ids");
     if (!g || !vecs || !out_ids || !query_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 1 || m > g->p.max_batch)
         return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
@@ -709,6 +722,7 @@ KNN_API knn_status knn_graph_query_ids(knn_graph *g, const float *vecs, int64_t 
 KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
                                                uint64_t query_id0, const int64_t *part_offsets, int32_t parts,
                                                int64_t *out_ids, float *out_sims, void *stream) {
+    NvtxRange nvtx_range("knn_graph_query_partitioned");
     if (!g || !vecs || !out_ids || !part_offsets) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 1 || m > g->p.max_batch)
         return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
@@ -819,6 +833,7 @@ KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, 
 }
 
 KNN_API knn_status knn_graph_remove(knn_graph *g, const int64_t *ids, int64_t m, void *stream) {
+    NvtxRange nvtx_range("knn_graph_remove");
     if (!g || (!ids && m > 0)) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 0) return fail(KNN_ERR_INVALID_ARG, "negative m");
     if (m == 0) return KNN_OK;
@@ -852,6 +867,7 @@ KNN_API knn_status knn_graph_remove(knn_graph *g, const int64_t *ids, int64_t m,
 
 KNN_API knn_status knn_graph_get_edges(knn_graph *g, int64_t *out_ids, float *out_sims, int64_t n_cap,
                                        int64_t *n_out, void *stream) {
+    NvtxRange nvtx_range("knn_graph_get_edges");
     if (!g || !out_ids || !n_out) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (n_cap < 0) return fail(KNN_ERR_INVALID_ARG, "negative n_cap");
     DeviceGuard dg(g->device);
@@ -951,6 +967,7 @@ KNN_API void knn_graph_destroy(knn_graph *g) {
 
 KNN_API knn_status knn_exact_graph(const float *X, int64_t n, int32_t dim, int32_t k, int64_t *out_ids,
                                    float *out_sims, void *stream) {
+    NvtxRange nvtx_range("knn_exact_graph");
     if (!X || !out_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (dim < 1 || dim > 256) return fail(KNN_ERR_UNSUPPORTED, "dim %d outside 1..256", dim);
     if (k < 1 || k > 32) return fail(KNN_ERR_UNSUPPORTED, "k %d outside 1..32", k);
@@ -1009,6 +1026,7 @@ KNN_API knn_status knn_balanced_kmedoids(const float *X, int64_t n, int32_t dim,
                                          double imbalance, int32_t chunks, int32_t iters,
                                          uint64_t seed, int32_t *out_labels, int64_t *out_medoids,
                                          int64_t *out_order, int64_t *out_offsets, void *stream) {
+    NvtxRange nvtx_range("knn_balanced_kmedoids");
     if (!X) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (dim < 1 || dim > 256) return fail(KNN_ERR_UNSUPPORTED, "dim %d outside 1..256", dim);
     if (p < 1 || p > KMED_MAX_P) return fail(KNN_ERR_UNSUPPORTED, "p %d outside 1..%d", p, KMED_MAX_P);
@@ -1086,6 +1104,11 @@ KNN_API knn_status knn_exact_set_path(int32_t path) {
     if (path != KNN_EXACT_AUTO && path != KNN_EXACT_CUDA_CORES && path != KNN_EXACT_TENSOR_CORES)
         return fail(KNN_ERR_INVALID_ARG, "unknown exact path %d", path);
     g_exact_path.store(path);
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_exact_set_wait_limit(int64_t ns) {
+    exact_tc_set_wait(ns);
     return KNN_OK;
 }
 
@@ -1260,6 +1283,7 @@ extern "C" {
 KNN_API knn_status knn_multi_create(const knn_params *params, int32_t graphs, const int64_t *n_init,
                                     const int64_t *capacity, const float *init_vecs, int32_t use_graph,
                                     void *stream, knn_multi **out) {
+    NvtxRange nvtx_range("knn_multi_create");
     if (!params || !n_init || !capacity || !init_vecs || !out) return fail(KNN_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (graphs < 1 || graphs > 65536) return fail(KNN_ERR_INVALID_ARG, "graphs %d outside 1..65536", graphs);
@@ -1351,6 +1375,7 @@ KNN_API knn_status knn_multi_create(const knn_params *params, int32_t graphs, co
 KNN_API knn_status knn_multi_step(knn_multi *mg, const float *vecs, const int32_t *graph, const int32_t *kind,
                                   const uint64_t *query_ids, int64_t m, int64_t *out_ids, float *out_sims,
                                   void *stream) {
+    NvtxRange nvtx_range("knn_multi_step");
     if (!mg || !vecs || !graph || !kind || !out_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 1 || m > mg->M) return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
     knn_graph *g = mg->g;

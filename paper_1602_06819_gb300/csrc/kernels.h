@@ -197,6 +197,8 @@ cudaError_t launch_exact(int dp, const ExactArgs &a, cudaStream_t s);
 // {largest norm, rows settled by brute force, wait-error bits}.  Reads the
 // number of unsettled rows back, so it synchronises the stream once.
 bool exact_tc_supported(int dp, int64_t n, int k, const uint32_t *removed);
+// pipeline wait limit of the tensor-core build in ns (< 0: the default)
+void exact_tc_set_wait(int64_t ns);
 size_t exact_tc_scratch_bytes(int64_t n, int dp);
 cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned **counters_out, cudaStream_t s);
 // snapshot restore: copy int64 lists (checking every id) and recompute their d2

@@ -100,7 +100,7 @@ __device__ __forceinline__ void offer_lanes(WarpTop<T> &top, unsigned lanes, uin
 }
 
 template <int STORAGE, int DP, int T, bool SMEM_VIS>
-__global__ void __launch_bounds__(SEARCH_WARPS * 32, 2)
+__global__ void __launch_bounds__(SEARCH_WARPS * 32, 8 / SEARCH_WARPS)
 ignns_search_kernel(const SearchArgs a) {
     using C = RowCfg<STORAGE, DP>;
     constexpr int NB = RowGather<STORAGE, DP>::ROWS;  // restart candidates per batch

@@ -49,6 +49,7 @@ EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "
             "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
             "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
+            "knn_exact_set_wait_limit",
             "knn_balanced_kmedoids", "knn_server_create", "knn_server_submit", "knn_server_wait",
             "knn_server_get_stats", "knn_server_destroy", "knn_multi_create", "knn_multi_step",
             "knn_multi_set_launch", "knn_multi_graph_size", "knn_multi_get_edges", "knn_multi_destroy",
@@ -136,6 +137,7 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_destroy": (None, [P]),
         "knn_exact_graph": (I32, [P, I64, I32, I32, P, P, P]),
         "knn_exact_set_path": (I32, [I32]),
+        "knn_exact_set_wait_limit": (I32, [I64]),
         "knn_server_create": (I32, [P, ctypes.POINTER(KnnServerParams), ctypes.POINTER(P)]),
         "knn_server_submit": (I32, [P, I32, P, I64, ctypes.POINTER(U64)]),
         "knn_server_wait": (I32, [P, U64, P, P, ctypes.POINTER(KnnRequestInfo)]),
@@ -333,6 +335,11 @@ def knn_balanced_kmedoids(X, p: int, imbalance: float, chunks: int, iters: int, 
 def knn_exact_set_path(path: str) -> None:
     """Process-wide choice of the exact-graph path: "auto", "cuda_cores" or "tensor_cores"."""
     _check(lib.knn_exact_set_path(EXACT_PATHS[path]), "knn_exact_set_path")
+
+
+def knn_exact_set_wait_limit(ns: int) -> None:
+    """Pipeline wait limit of the tensor-core build (ns < 0: default 2 s)."""
+    _check(lib.knn_exact_set_wait_limit(int(ns)), "knn_exact_set_wait_limit")
 
 
 def knn_exact_last_info() -> dict:

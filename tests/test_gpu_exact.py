@@ -136,3 +136,27 @@ def test_exact_graph_full_size_sampled_rows(knn):
     srt = np.sort(ids, axis=1)
     assert not np.any(srt[:, 1:] == srt[:, :-1])
     assert np.all(np.diff(sims, axis=1) <= 0)
+
+
+def test_exact_tensor_cores_wait_timeouts_are_detected_and_harmless(knn):
+    """Failure detection without a fault: with a zero wait limit the
+    pipeline roles give up on each other, the wait errors are reported, and
+    the FP32 pass recomputes the affected rows, so the lists stay exact."""
+    X = Mixture(d=64, components=6, half_width=10.0, sigma=1.0, seed=21).sample(1500, 2)
+    knn.knn_exact_set_wait_limit(0)
+    try:
+        import torch
+        out = torch.empty((1500, 10), dtype=torch.int64, device="cuda")
+        osims = torch.empty((1500, 10), dtype=torch.float32, device="cuda")
+        knn.knn_exact_set_path("tensor_cores")
+        knn.knn_exact_graph(cuda_tensor(X), 10, out, osims)
+        torch.cuda.synchronize()
+        info = knn.knn_exact_last_info()
+    finally:
+        knn.knn_exact_set_wait_limit(-1)
+        knn.knn_exact_set_path("auto")
+    assert info["path"] == "tensor_cores" and info["wait_errors"] != 0 and info["rows_redone"] > 0
+    o_ids, o_sims, margin = oracle.exact_knn(X, 10)
+    check_rows(out.cpu().numpy(), osims.cpu().numpy(), o_ids, o_sims, margin, exact_tol(64))
+    ids, _ = gpu_exact(knn, X, 10, "tensor_cores")   # the default limit again: no errors
+    assert knn.knn_exact_last_info()["wait_errors"] == 0
