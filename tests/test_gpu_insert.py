@@ -182,3 +182,33 @@ def test_full_size_batch_properties(knn):
         want = [oracle.similarity(X[u], X[v]) for v in ids[u]]
         assert rel_err(sims[u], want).max() <= 1e-5
         assert np.all(np.diff(sims[u]) <= 0)
+
+
+@pytest.mark.parametrize("m", [64, 1000])
+def test_hub_node_under_contention(knn, m):
+    """The lock-free Update under contention: m points of one batch placed
+    right next to node w (exhaustive search, so w is in every point's level
+    1) all offer themselves to w at once through its atomicExch chain; the
+    merged list of w must be the best k of its old list and the m points
+    (Algorithm 2's "if needed, add new" applied in any order)."""
+    import torch
+    mix = Mixture(d=32, components=5, half_width=10.0, sigma=1.0, seed=19)
+    n0, k = 1500, 10
+    X0 = mix.sample(n0, 1)
+    o_ids, _, _ = oracle.exact_knn(X0, k)
+    w = 777
+    rng = np.random.default_rng(5)
+    pts = (X0[w] + 0.01 * rng.standard_normal((m, 32))).astype(np.float32)
+    g = make_graph(knn, X0, k, 1.0, math.inf, 3, n0 + m, max_batch=m, nbr_ids=o_ids)
+    try:
+        g.insert(cuda_tensor(pts))
+        lists, _ = edges(g, n0 + m, k)
+    finally:
+        g.close()
+    allx = np.concatenate([X0, pts]).astype(np.float64)
+    cand = np.concatenate([o_ids[w], np.arange(n0, n0 + m)])
+    d = np.linalg.norm(allx[cand] - allx[w], axis=1)
+    want = cand[np.lexsort((cand, d))][:k]
+    assert list(lists[w]) == list(want)
+    # and every new point's own list holds w or points of the batch only
+    assert np.all((lists[n0:] == w) | (lists[n0:] >= n0))
