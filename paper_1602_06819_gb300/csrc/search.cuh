@@ -115,6 +115,8 @@ ignns_search_kernel(const SearchArgs a) {
     const int nwarps = gridDim.x * SEARCH_WARPS;
     const float INF = __int_as_float(0x7f800000);
     const bool multi = a.seg.item_seg != nullptr;
+    // no removed node: skip the bitset reads
+    const bool any_removed = a.n_live < (int64_t)a.n || a.parts > 1;
     // climb list prefetch: lane l holds entry pf_p of the list of neighbour
     // pf_j, for the first npf = floor(32 / k) neighbours
     const int npf = 32 / a.k;
@@ -178,7 +180,7 @@ ignns_search_kernel(const SearchArgs a) {
                 const uint64_t jj = j + (uint64_t)lane;
                 const bool valid = jj < max_draws;
                 const uint32_t r = valid ? lo + restart_node(rkey, jj, np) : lo;
-                const bool good = valid && !test_bit_ro(a.removed, r) && !vis.test(r);
+                const bool good = valid && !(any_removed && test_bit_ro(a.removed, r)) && !vis.test(r);
                 const unsigned bal = __ballot_sync(FULL, good);
                 const int avail = __popc(bal);
                 const int take = avail < want - nc ? avail : want - nc;
@@ -269,7 +271,8 @@ ignns_search_kernel(const SearchArgs a) {
                 while (true) {
                     ++adj;
                     // a partition follows only its own nodes (Algorithm 3)
-                    const bool valid = nb >= 0 && (uint32_t)nb - lo < np && !test_bit_ro(a.removed, (uint32_t)nb);
+                    const bool valid = nb >= 0 && (uint32_t)nb - lo < np &&
+                                       !(any_removed && test_bit_ro(a.removed, (uint32_t)nb));
                     __syncwarp();
                     const bool seen = valid && vis.test((uint32_t)nb);
                     // the lists of the first 32 / k neighbours load in the same
