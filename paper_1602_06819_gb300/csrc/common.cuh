@@ -132,10 +132,14 @@ struct WarpTop {
 // so each load instruction of the group covers G*16 contiguous bytes.  RPP =
 // 32/G rows are read per pass and P passes are kept in flight.
 //
-// FP32 arithmetic: a lane accumulates its CPL*E products with fused
-// multiply-adds in element order, then the group adds its partial sums in a
-// log2(G)-level butterfly.  The relative error of a squared distance is thus
-// at most about (CPL*E + log2(G) + 1) units of 2^-24.
+// FP32 arithmetic: FP32 and BF16 rows keep four running sums per lane (two
+// packed FP32 pairs), each adding every fourth of the lane's e = CPL*E
+// squared differences with fused multiply-adds; the lane then adds its four
+// sums in two levels and the group adds its partial sums in a log2(G)-level
+// butterfly.  With the rounding of each difference, the relative error of a
+// squared distance is at most about (e/4 + log2(G) + 4) units of 2^-24.  FP8
+// rows keep one running sum in element order: (e + log2(G) + 5) units, the
+// product with the row scale included.
 // ---------------------------------------------------------------------------
 template <int STORAGE, int DP>
 struct RowCfg {
@@ -241,6 +245,60 @@ __device__ __forceinline__ float chunk_d2(uint4 w, const float *qv, float scale,
     return acc;
 }
 
+// Packed FP32 pairs (sm_100 and later): each half is an IEEE binary32
+// operation rounded to nearest, two per instruction.
+__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+// acc + (q - x)^2 on both halves, the difference rounded before the fma
+__device__ __forceinline__ unsigned long long f32x2_sqdiff_acc(unsigned long long q, unsigned long long x,
+                                                               unsigned long long acc) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(q), "l"(x));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(acc) : "l"(d), "l"(acc));
+    return acc;
+}
+// (a.lo + b.lo) + (a.hi + b.hi)
+__device__ __forceinline__ float f32x2_total(unsigned long long a, unsigned long long b) {
+    unsigned long long s;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s) : "l"(a), "l"(b));
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(s));
+    return lo + hi;
+}
+
+// A lane's partial squared distance over its chunks of one row.
+template <int STORAGE>
+struct RowAcc {
+    float acc = 0.0f;
+    __device__ __forceinline__ void add(uint4 w, const float *qv, float scale) {
+        acc = chunk_d2<STORAGE>(w, qv, scale, acc);
+    }
+    __device__ __forceinline__ float total() const { return acc; }
+};
+template <>
+struct RowAcc<ST_FP32> {
+    unsigned long long a = 0ull, b = 0ull;  // +0.0f in both halves
+    __device__ __forceinline__ void add(uint4 w, const float *qv, float) {
+        a = f32x2_sqdiff_acc(f32x2_pack(qv[0], qv[1]), f32x2_pack(__uint_as_float(w.x), __uint_as_float(w.y)), a);
+        b = f32x2_sqdiff_acc(f32x2_pack(qv[2], qv[3]), f32x2_pack(__uint_as_float(w.z), __uint_as_float(w.w)), b);
+    }
+    __device__ __forceinline__ float total() const { return f32x2_total(a, b); }
+};
+template <>
+struct RowAcc<ST_BF16> {
+    unsigned long long a = 0ull, b = 0ull;
+    __device__ __forceinline__ void add(uint4 w, const float *qv, float) {
+        a = f32x2_sqdiff_acc(f32x2_pack(qv[0], qv[1]), f32x2_pack(bf16_lo(w.x), bf16_hi(w.x)), a);
+        b = f32x2_sqdiff_acc(f32x2_pack(qv[2], qv[3]), f32x2_pack(bf16_lo(w.y), bf16_hi(w.y)), b);
+        a = f32x2_sqdiff_acc(f32x2_pack(qv[4], qv[5]), f32x2_pack(bf16_lo(w.z), bf16_hi(w.z)), a);
+        b = f32x2_sqdiff_acc(f32x2_pack(qv[6], qv[7]), f32x2_pack(bf16_lo(w.w), bf16_hi(w.w)), b);
+    }
+    __device__ __forceinline__ float total() const { return f32x2_total(a, b); }
+};
+
 // Row gathers split in two: issue() starts the loads of up to ROWS rows
 // (lane c < nrows holds row id rid) and reduce() waits for them, leaving the
 // squared distance of row c in lane c.  Work placed between the two calls
@@ -256,22 +314,21 @@ struct RowGather {
     uint4 buf[C::P][C::CPL];
     float scl[C::P];
 
+    // Every pass loads (a group past the last row re-reads the row of lane
+    // 0, whose rid must be a valid row even for nrows = 0; the result is
+    // dropped), so that reduce() runs straight through and the arithmetic of
+    // the passes interleaves.
     __device__ __forceinline__ void issue(const RowSource &src, uint32_t rid, int nrows) {
         const int lane = threadIdx.x & 31;
         const int gl = lane / C::G, gi = lane % C::G;
 #pragma unroll
         for (int p = 0; p < C::P; ++p) {
             const int c = p * C::RPP + gl;
-            const uint32_t row = __shfl_sync(FULL, rid, c & 31);
-            const bool act = c < nrows;
+            const uint32_t row = __shfl_sync(FULL, rid, c < nrows ? (c & 31) : 0);
             const uint4 *base = reinterpret_cast<const uint4 *>(src.rows + (size_t)row * C::ROW_BYTES);
 #pragma unroll
-            for (int k = 0; k < C::CPL; ++k) {
-                buf[p][k] = make_uint4(0, 0, 0, 0);
-                if (act) buf[p][k] = ld_nc_v4(base + gi + k * C::G);
-            }
-            scl[p] = 1.0f;
-            if (STORAGE == ST_FP8 && act) scl[p] = __uint_as_float(ld_nc_u32(src.scale + row));
+            for (int k = 0; k < C::CPL; ++k) buf[p][k] = ld_nc_v4(base + gi + k * C::G);
+            scl[p] = STORAGE == ST_FP8 ? __uint_as_float(ld_nc_u32(src.scale + row)) : 1.0f;
         }
     }
 
@@ -280,10 +337,10 @@ struct RowGather {
         float result = __int_as_float(0x7f800000);
 #pragma unroll
         for (int p = 0; p < C::P; ++p) {
-            if (p * C::RPP >= nrows) break;  // warp-uniform: no rows left
-            float acc = 0.0f;
+            RowAcc<STORAGE> ra;
 #pragma unroll
-            for (int k = 0; k < C::CPL; ++k) acc = chunk_d2<STORAGE>(buf[p][k], qv + k * C::E, scl[p], acc);
+            for (int k = 0; k < C::CPL; ++k) ra.add(buf[p][k], qv + k * C::E, scl[p]);
+            float acc = ra.total();
 #pragma unroll
             for (int off = C::G / 2; off >= 1; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
             const int c = lane - p * C::RPP;
@@ -330,9 +387,10 @@ __device__ __forceinline__ float gather_d2(const RowSource &src, uint32_t rid, i
 #pragma unroll
         for (int p = 0; p < C::P; ++p) {
             if ((p0 + p) * C::RPP >= nrows) break;  // warp-uniform: no rows left
-            float acc = 0.0f;
+            RowAcc<STORAGE> ra;
 #pragma unroll
-            for (int k = 0; k < C::CPL; ++k) acc = chunk_d2<STORAGE>(buf[p][k], qv + k * C::E, scl[p], acc);
+            for (int k = 0; k < C::CPL; ++k) ra.add(buf[p][k], qv + k * C::E, scl[p]);
+            float acc = ra.total();
 #pragma unroll
             for (int off = C::G / 2; off >= 1; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
             // row c = (p0+p)*RPP + g is held by the lanes of group g

@@ -6,13 +6,15 @@ test, a climb, the order of two list entries) can legitimately go the other
 way on the GPU only when the oracle's relative margin for it is below what
 FP32 rounding can move.  The bounds follow the kernels' summation order:
 
-* row gathers (search, update, cross, re-score): a lane adds its e = DP/G
-  products with fused multiply-adds, then log2(G) butterfly steps; with the
-  rounding of each difference the relative error of d2 is at most
-  (e + log2(G) + 3) u, u = 2^-24.  A similarity 1/(1 + sqrt(d2)) adds about
-  3 u more, e (the expansion) is rounded to FP32 (u).  A comparison cannot
-  flip when the margin exceeds eps_d2 + 8 u; the tests flag margins below
-  twice that.
+* row gathers (search, update, cross, re-score): a lane holds e = DP/G
+  elements of a row.  FP32 and BF16 rows: four running sums of e/4 squared
+  differences each (fused multiply-adds), added in two levels, then log2(G)
+  butterfly steps; with the rounding of each difference the relative error
+  of d2 is at most (e/4 + log2(G) + 4) u, u = 2^-24.  FP8 rows: one running
+  sum of e products and the rounding of the scaled value,
+  (e + log2(G) + 5) u.  A similarity 1/(1 + sqrt(d2)) adds about 3 u more,
+  e (the expansion) is rounded to FP32 (u).  A comparison cannot flip when
+  the margin exceeds eps_d2 + 8 u; the tests flag margins below twice that.
 * the exact-graph kernel adds all DP products of a pair in order:
   eps_d2 <= (DP + 2) u, flagged below 2 (DP + 10) u.
 
@@ -43,7 +45,10 @@ def gather_tol(d: int, storage: int = 0) -> float:
     nc = dp // e
     g = _group(nc)
     per_lane = dp // g
-    eps = (per_lane + math.log2(g) + 3 + (2 if storage == 2 else 0)) * U
+    if storage == 2:
+        eps = (per_lane + math.log2(g) + 5) * U
+    else:
+        eps = (per_lane / 4 + math.log2(g) + 4) * U
     return 2.0 * (eps + 8 * U)
 
 
