@@ -351,12 +351,13 @@ struct RowGather {
     }
 };
 
-// The row layout with at most MAX_ROWS rows in flight.
+// The row layout with passes for MAX_ROWS rows (rounded up to whole passes)
+// in flight.
 template <int STORAGE, int DP, int MAX_ROWS>
 struct GatherCfg : RowCfg<STORAGE, DP> {
     using C0 = RowCfg<STORAGE, DP>;
-    static constexpr int P = C0::P * C0::RPP <= MAX_ROWS ? C0::P
-                             : (MAX_ROWS / C0::RPP > 0 ? MAX_ROWS / C0::RPP : 1);
+    static constexpr int NEED = (MAX_ROWS + C0::RPP - 1) / C0::RPP;
+    static constexpr int P = NEED < C0::P ? NEED : C0::P;
 };
 
 // MAX_ROWS bounds the rows in flight at once (and the registers they take).
@@ -386,7 +387,9 @@ __device__ __forceinline__ float gather_d2(const RowSource &src, uint32_t rid, i
         }
 #pragma unroll
         for (int p = 0; p < C::P; ++p) {
-            if ((p0 + p) * C::RPP >= nrows) break;  // warp-uniform: no rows left
+            // a gather sized to its rows (MAX_ROWS < 32) reduces every pass,
+            // straight through (passes without rows hold zeros)
+            if (MAX_ROWS >= 32 && (p0 + p) * C::RPP >= nrows) break;  // warp-uniform
             RowAcc<STORAGE> ra;
 #pragma unroll
             for (int k = 0; k < C::CPL; ++k) ra.add(buf[p][k], qv + k * C::E, scl[p]);

@@ -12,8 +12,10 @@
 // decisions need to be taken one at a time:
 //
 // * Restarts.  The similarity of a drawn node does not depend on the search
-//   state, so the warp draws up to 32 unvisited candidates ahead and gathers
-//   their rows together (16-byte coalesced loads, all in flight at once).
+//   state, so the warp draws batches of up to 32 unvisited candidates ahead
+//   and gathers a batch's rows together (16-byte coalesced loads, all in
+//   flight at once): while one batch is decided the next one loads and the
+//   one after it is drawn.
 //   Between two accepted restarts the search only counts, marks and offers:
 //   one ballot finds the first candidate the expansion test keeps, and every
 //   candidate before it is committed at once (a discarded restart cannot
@@ -169,6 +171,25 @@ ignns_search_kernel(const SearchArgs a) {
         uint64_t j = 0;
         float d2min = INF;  // s_max = sim_of_d2(d2min); none while d2min is +inf
         float thr = 0.0f;   // s_max / e
+        // Squared distances below lo2 surely pass the expansion test and
+        // those above hi2 surely fail it; only the band between evaluates
+        // sim(q, r) < s_max / e itself.  The FP32 similarity errs by a few
+        // units of 2^-24 and the band is 2^-12 wide on each side of the
+        // boundary ((1 / thr - 1)^2, at least 1 when thr <= 1/2); above 1/2,
+        // or past 2^100, every candidate takes the exact test.
+        float lo2 = -1.0f, hi2 = INF;
+        auto set_best = [&](float d2) {
+            d2min = d2;
+            thr = sim_of_d2(d2) / a.expansion;
+            const float sb = 1.0f / thr - 1.0f;
+            if (thr <= 0.5f && sb * sb < 0x1p100f) {
+                lo2 = sb * sb * (1.0f - 0x1p-12f);
+                hi2 = sb * sb * (1.0f + 0x1p-12f);
+            } else {
+                lo2 = -1.0f;
+                hi2 = INF;
+            }
+        };
         bool done = limit <= 0;
 
         // Draw up to `want` candidates after draw j, skipping nodes visited or
@@ -206,29 +227,32 @@ ignns_search_kernel(const SearchArgs a) {
         };
         auto cap = [&](int room) -> int { return room < NB ? room : NB; };
 
-        // Batch A is decided while the rows of the next batch B load.
+        // Batch A is decided while the rows of the next batch B load, and the
+        // ids of the batch after B (C) are drawn meanwhile: B's loads start
+        // as soon as A is settled.
         RowGather<STORAGE, DP> G;
-        uint32_t aid = 0xffffffffu;
-        uint64_t aj = 0;
+        uint32_t aid = 0xffffffffu, bid = 0xffffffffu;
+        uint64_t aj = 0, bj = 0;
         int an = done ? 0 : draw(cap(limit), aid, aj);
         float ad2 = __int_as_float(0x7f800000);
         if (an > 0) {
             G.issue(src, lane < an ? aid : 0u, an);
             ad2 = G.reduce(an, qv);
         }
+        int bn = an > 0 && limit - an > 0 ? draw(cap(limit - an), bid, bj) : 0;
         while (an > 0) {
-            // ---- draw B (filtered by the marks so far) and start its loads
-            uint32_t bid = 0xffffffffu;
-            uint64_t bj = 0;
-            const int room = limit - evals - an;
-            int bn = room > 0 ? draw(cap(room), bid, bj) : 0;
-            // issue and reduce are paired unconditionally (no loads for bn = 0),
-            // so the row buffer is visibly dead after the reduce
+            // ---- start B's loads, then draw C (filtered by the marks so far).
+            // issue and reduce are paired unconditionally, so the row buffer
+            // is visibly dead after the reduce
             G.issue(src, lane < bn ? bid : 0u, bn);
+            uint32_t cid = 0xffffffffu;
+            uint64_t cj = 0;
+            const int room = limit - evals - an - bn;
+            const int cn = room > 0 ? draw(cap(room), cid, cj) : 0;
 
-            // ---- decide A, in draw order.  A was filtered before the batch
-            // before it was decided: re-test its candidates; an earlier copy of
-            // the same node in A makes a candidate a redraw.
+            // ---- decide A, in draw order.  A was filtered before the two
+            // batches before it were decided: re-test its candidates; an
+            // earlier copy of the same node in A makes a candidate a redraw.
             const uint64_t akey = pack_key(ad2, aid);
             const unsigned same = __match_any_sync(FULL, aid);
             unsigned skip = __ballot_sync(FULL, lane >= an || (same & lt_mask) != 0u || vis.test(aid));
@@ -240,9 +264,11 @@ ignns_search_kernel(const SearchArgs a) {
                 unsigned ev = ~skip & (FULL << start);
                 if (ev == 0u) return 32;
                 ev = lowest_bits(ev, limit - evals);
-                bool keep = false;
-                if ((ev >> lane) & 1u)
-                    keep = !a.discard || !(d2min < INF) || !(sim_of_d2(ad2) < thr);
+                const bool in = (ev >> lane) & 1u;
+                bool keep = in && (!a.discard || !(d2min < INF) || ad2 <= lo2);
+                const bool band = in && !keep && !(ad2 >= hi2);
+                if (__any_sync(FULL, band))  // rare: the exact test
+                    keep |= band && !(sim_of_d2(ad2) < thr);
                 const unsigned kept = __ballot_sync(FULL, keep);
                 const int ai = kept ? __ffs(kept) - 1 : 32;
                 const unsigned evm = ai < 32 ? (ev & upto(ai)) : ev;
@@ -255,19 +281,25 @@ ignns_search_kernel(const SearchArgs a) {
                 offer_lanes(top, evm, akey);
                 return ai;
             };
+            // the list of a kept restart (lanes < k), loaded as soon as it is kept
+            auto list_of = [&](int i) -> int32_t {
+                const uint32_t r = __shfl_sync(FULL, aid, i);
+                return lane < a.k ? (int32_t)ld_nc_u32(a.nbr + (size_t)r * a.k + lane) : -1;
+            };
             int ai = segment(0);
+            int32_t nbk = ai < 32 ? list_of(ai) : -1;
             // B's distances, before any climb (one row buffer is live at a time)
             const float bd2 = G.reduce(bn, qv);
 
             while (ai < 32) {
                 const float d2a = __shfl_sync(FULL, ad2, ai);
-                if (d2a < d2min) { d2min = d2a; thr = sim_of_d2(d2min) / a.expansion; }
+                if (d2a < d2min) set_best(d2a);
                 if (evals >= limit) { done = true; break; }
 
                 // ---- eager hill climbing from the kept restart
                 uint32_t cur = __shfl_sync(FULL, aid, ai);
                 float d2cur = d2a;
-                int32_t nb = lane < a.k ? (int32_t)ld_nc_u32(a.nbr + (size_t)cur * a.k + lane) : -1;
+                int32_t nb = nbk;
                 while (true) {
                     ++adj;
                     // a partition follows only its own nodes (Algorithm 3)
@@ -280,7 +312,11 @@ ignns_search_kernel(const SearchArgs a) {
                     // pf_j), so a move to one of them needs no list load
                     const int32_t nbj = __shfl_sync(FULL, nb, pf_j);
                     const int32_t pfl = (pf_j < npf && nbj >= 0) ? (int32_t)ld_nc_u32(a.nbr + (size_t)nbj * a.k + pf_p) : -1;
-                    const float nd2 = gather_d2<STORAGE, DP>(src, valid ? (uint32_t)nb : 0u, a.k, qv);
+                    // as many passes as the k rows need (one pass holds 32 / G rows)
+                    const uint32_t nrow = valid ? (uint32_t)nb : 0u;
+                    const float nd2 = a.k <= 12   ? gather_d2<STORAGE, DP, 12>(src, nrow, a.k, qv)
+                                      : a.k <= 24 ? gather_d2<STORAGE, DP, 24>(src, nrow, a.k, qv)
+                                                  : gather_d2<STORAGE, DP>(src, nrow, a.k, qv);
                     unsigned um = __ballot_sync(FULL, valid && !seen);
                     if (um == 0u) break;  // every neighbour visited: local maximum
                     um = lowest_bits(um, limit - evals);
@@ -309,10 +345,12 @@ ignns_search_kernel(const SearchArgs a) {
                     const bool mine = (evc >> lane) & 1u;
                     if (mine) vis.mark((uint32_t)nb);
                     offer_lanes(top, evc, pack_key(nd2, (uint32_t)nb));
-                    float mn = mine ? nd2 : INF;
+                    if (__any_sync(FULL, mine && nd2 < d2min)) {  // a new best: s_max rises
+                        float mn = mine ? nd2 : INF;
 #pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1) mn = fminf(mn, __shfl_xor_sync(FULL, mn, off));
-                    if (mn < d2min) { d2min = mn; thr = sim_of_d2(d2min) / a.expansion; }
+                        for (int off = 16; off >= 1; off >>= 1) mn = fminf(mn, __shfl_xor_sync(FULL, mn, off));
+                        set_best(mn);
+                    }
                     if (mi < 32) ++moves;
                     if (evals >= limit) { done = true; break; }
                     if (mi == 32) break;  // no unvisited neighbour is more similar
@@ -330,23 +368,33 @@ ignns_search_kernel(const SearchArgs a) {
                 __syncwarp();
                 skip |= __ballot_sync(FULL, lane > ai && lane < an && vis.test(aid));
                 ai = ai + 1 < 32 ? segment(ai + 1) : 32;
+                if (ai < 32) nbk = list_of(ai);
             }
             if (evals >= limit) done = true;
             if (done) break;
-            if (bn == 0) {  // B was not drawn ahead (the budget looked spent)
-                bn = draw(cap(limit - evals), bid, bj);
-                if (bn == 0) break;
-                G.issue(src, lane < bn ? bid : 0u, bn);
-                aid = bid;
-                aj = bj;
-                an = bn;
-                ad2 = G.reduce(bn, qv);
+            if (bn == 0) {
+                // B is empty (the budget looked spent when it was drawn): C,
+                // else a new draw, becomes A and loads now
+                if (cn > 0) {
+                    aid = cid;
+                    aj = cj;
+                    an = cn;
+                } else {
+                    an = draw(cap(limit - evals), aid, aj);
+                    if (an == 0) break;
+                }
+                G.issue(src, lane < an ? aid : 0u, an);
+                ad2 = G.reduce(an, qv);
+                bn = limit - evals - an > 0 ? draw(cap(limit - evals - an), bid, bj) : 0;
                 continue;
             }
             aid = bid;
             aj = bj;
             an = bn;
             ad2 = bd2;
+            bid = cid;
+            bj = cj;
+            bn = cn;
         }
 
         // ---- results and counters
