@@ -361,6 +361,9 @@ struct GatherCfg : RowCfg<STORAGE, DP> {
 };
 
 // MAX_ROWS bounds the rows in flight at once (and the registers they take).
+// Lane c < nrows holds the id of row c, or GATHER_SKIP for a row that is not
+// loaded (its result is meaningless).
+constexpr uint32_t GATHER_SKIP = 0xffffffffu;
 template <int STORAGE, int DP, int MAX_ROWS = 32>
 __device__ __forceinline__ float gather_d2(const RowSource &src, uint32_t rid, int nrows,
                                            const float (&qv)[RowCfg<STORAGE, DP>::QF]) {
@@ -375,7 +378,7 @@ __device__ __forceinline__ float gather_d2(const RowSource &src, uint32_t rid, i
         for (int p = 0; p < C::P; ++p) {
             const int c = (p0 + p) * C::RPP + gl;
             const uint32_t row = __shfl_sync(FULL, rid, c & 31);
-            const bool act = c < nrows;
+            const bool act = c < nrows && row != GATHER_SKIP;
             const uint4 *base = reinterpret_cast<const uint4 *>(src.rows + (size_t)row * C::ROW_BYTES);
 #pragma unroll
             for (int k = 0; k < C::CPL; ++k) {

@@ -470,6 +470,14 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
         CU(cudaMemsetAsync(g->counters, 0, (size_t)M * NCTR * 8, s));
         CU(launch_fill_i32(g->head, -1, C, s));
         CU(launch_fill_i32(g->nbr_ids, -1, C * K, s));
+        // an empty search launch resolves the search kernels of this graph's
+        // storage and dimension (both top-list sizes), so that lazy module
+        // loading does not land inside the first search
+        SearchArgs none{};
+        none.KT = 1;
+        CU(launch_search(g->p.storage, g->dp, none, s));
+        none.KT = 33;
+        CU(launch_search(g->p.storage, g->dp, none, s));
         return KNN_OK;
     };
     st = fills();

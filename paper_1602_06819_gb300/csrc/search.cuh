@@ -167,7 +167,7 @@ ignns_search_kernel(const SearchArgs a) {
         WarpTop<T> top;
         top.init(a.KT);
         int evals = 0, restarts = 0, discarded = 0, moves = 0, adj = 0;  // budgets are < 2^31
-        unsigned long long draws_used = 0;
+        unsigned long long jlast = 0;  // this lane's latest committed draw index + 1
         uint64_t j = 0;
         float d2min = INF;  // s_max = sim_of_d2(d2min); none while d2min is +inf
         float thr = 0.0f;   // s_max / e
@@ -193,29 +193,38 @@ ignns_search_kernel(const SearchArgs a) {
         bool done = limit <= 0;
 
         // Draw up to `want` candidates after draw j, skipping nodes visited or
-        // removed (free redraws); lane c < count receives candidate c.
-        auto draw = [&](int want, uint32_t &id, uint64_t &dj) -> int {
+        // removed (free redraws); lane c < count receives candidate c, and
+        // `same` the lanes holding the same node.  A round looks at 64 draws,
+        // two per lane (j + lane and j + 32 + lane).
+        auto draw = [&](int want, uint32_t &id, uint64_t &dj, unsigned &same) -> int {
             int nc = 0;
             __syncwarp();  // marks made so far are visible to the bit reads
             while (nc < want && j < max_draws) {
-                const uint64_t jj = j + (uint64_t)lane;
-                const bool valid = jj < max_draws;
-                const uint32_t r = valid ? lo + restart_node(rkey, jj, np) : lo;
-                const bool good = valid && !(any_removed && test_bit_ro(a.removed, r)) && !vis.test(r);
-                const unsigned bal = __ballot_sync(FULL, good);
-                const int avail = __popc(bal);
+                const uint64_t j0 = j + (uint64_t)lane, j1 = j0 + 32u;
+                const bool v0 = j0 < max_draws, v1 = j1 < max_draws;
+                const uint32_t r0 = v0 ? lo + restart_node(rkey, j0, np) : lo;
+                const uint32_t r1 = v1 ? lo + restart_node(rkey, j1, np) : lo;
+                const bool g0 = v0 && !(any_removed && test_bit_ro(a.removed, r0)) && !vis.test(r0);
+                const bool g1 = v1 && !(any_removed && test_bit_ro(a.removed, r1)) && !vis.test(r1);
+                const unsigned b0 = __ballot_sync(FULL, g0), b1 = __ballot_sync(FULL, g1);
+                const int a0 = __popc(b0), avail = a0 + __popc(b1);
                 const int take = avail < want - nc ? avail : want - nc;
-                const int rank = __popc(bal & lt_mask);
-                if (good && rank < take) {
-                    s_id[wib][nc + rank] = r;
-                    s_j[wib][nc + rank] = jj;
+                const int k0 = __popc(b0 & lt_mask), k1 = a0 + __popc(b1 & lt_mask);
+                if (g0 && k0 < take) {
+                    s_id[wib][nc + k0] = r0;
+                    s_j[wib][nc + k0] = j0;
+                }
+                if (g1 && k1 < take) {
+                    s_id[wib][nc + k1] = r1;
+                    s_j[wib][nc + k1] = j1;
                 }
                 if (take > 0 && take < avail) {
                     // batch full: resume after the last draw taken
-                    const int last = __ffs(__ballot_sync(FULL, good && rank == take - 1)) - 1;
-                    j += (uint64_t)last + 1u;
+                    const unsigned lb = take <= a0 ? __ballot_sync(FULL, g0 && k0 == take - 1)
+                                                   : __ballot_sync(FULL, g1 && k1 == take - 1);
+                    j += (uint64_t)(__ffs(lb) - 1 + (take <= a0 ? 0 : 32)) + 1u;
                 } else {
-                    j += 32u;
+                    j += 64u;
                 }
                 if (j > max_draws) j = max_draws;
                 nc += take;
@@ -223,6 +232,7 @@ ignns_search_kernel(const SearchArgs a) {
             __syncwarp();
             id = lane < nc ? s_id[wib][lane] : 0xffffffffu;
             dj = lane < nc ? s_j[wib][lane] : 0ull;
+            same = __match_any_sync(FULL, id);  // used a batch or two later
             return nc;
         };
         auto cap = [&](int room) -> int { return room < NB ? room : NB; };
@@ -233,13 +243,14 @@ ignns_search_kernel(const SearchArgs a) {
         RowGather<STORAGE, DP> G;
         uint32_t aid = 0xffffffffu, bid = 0xffffffffu;
         uint64_t aj = 0, bj = 0;
-        int an = done ? 0 : draw(cap(limit), aid, aj);
+        unsigned asame = 0u, bsame = 0u;
+        int an = done ? 0 : draw(cap(limit), aid, aj, asame);
         float ad2 = __int_as_float(0x7f800000);
         if (an > 0) {
             G.issue(src, lane < an ? aid : 0u, an);
             ad2 = G.reduce(an, qv);
         }
-        int bn = an > 0 && limit - an > 0 ? draw(cap(limit - an), bid, bj) : 0;
+        int bn = an > 0 && limit - an > 0 ? draw(cap(limit - an), bid, bj, bsame) : 0;
         while (an > 0) {
             // ---- start B's loads, then draw C (filtered by the marks so far).
             // issue and reduce are paired unconditionally, so the row buffer
@@ -247,15 +258,15 @@ ignns_search_kernel(const SearchArgs a) {
             G.issue(src, lane < bn ? bid : 0u, bn);
             uint32_t cid = 0xffffffffu;
             uint64_t cj = 0;
+            unsigned csame = 0u;
             const int room = limit - evals - an - bn;
-            const int cn = room > 0 ? draw(cap(room), cid, cj) : 0;
+            const int cn = room > 0 ? draw(cap(room), cid, cj, csame) : 0;
 
             // ---- decide A, in draw order.  A was filtered before the two
             // batches before it were decided: re-test its candidates; an
             // earlier copy of the same node in A makes a candidate a redraw.
             const uint64_t akey = pack_key(ad2, aid);
-            const unsigned same = __match_any_sync(FULL, aid);
-            unsigned skip = __ballot_sync(FULL, lane >= an || (same & lt_mask) != 0u || vis.test(aid));
+            unsigned skip = __ballot_sync(FULL, lane >= an || (asame & lt_mask) != 0u || vis.test(aid));
             // Commit the candidates from `start` up to the first one the
             // expansion test keeps (all are kept while no s_max exists);
             // returns that candidate, or 32 when every candidate left was
@@ -276,8 +287,10 @@ ignns_search_kernel(const SearchArgs a) {
                 evals += ne;
                 restarts += ne;
                 discarded += ne - (ai < 32 ? 1 : 0);
-                draws_used = shfl_u64(aj, 31 - __clz(evm)) + 1ull;
-                if ((evm >> lane) & 1u) vis.mark(aid);
+                if ((evm >> lane) & 1u) {
+                    vis.mark(aid);
+                    jlast = aj + 1ull;  // draw indexes grow: the last commit is the largest
+                }
                 offer_lanes(top, evm, akey);
                 return ai;
             };
@@ -307,19 +320,20 @@ ignns_search_kernel(const SearchArgs a) {
                                        !(any_removed && test_bit_ro(a.removed, (uint32_t)nb));
                     __syncwarp();
                     const bool seen = valid && vis.test((uint32_t)nb);
+                    unsigned um = __ballot_sync(FULL, valid && !seen);
+                    if (um == 0u) break;  // every neighbour visited: local maximum
+                    um = lowest_bits(um, limit - evals);
                     // the lists of the first 32 / k neighbours load in the same
                     // round trip as their rows (lane l: entry pf_p of neighbour
                     // pf_j), so a move to one of them needs no list load
                     const int32_t nbj = __shfl_sync(FULL, nb, pf_j);
                     const int32_t pfl = (pf_j < npf && nbj >= 0) ? (int32_t)ld_nc_u32(a.nbr + (size_t)nbj * a.k + pf_p) : -1;
-                    // as many passes as the k rows need (one pass holds 32 / G rows)
-                    const uint32_t nrow = valid ? (uint32_t)nb : 0u;
+                    // only the rows the step can evaluate load; as many passes
+                    // as the k rows need (one pass holds 32 / G rows)
+                    const uint32_t nrow = ((um >> lane) & 1u) ? (uint32_t)nb : GATHER_SKIP;
                     const float nd2 = a.k <= 12   ? gather_d2<STORAGE, DP, 12>(src, nrow, a.k, qv)
                                       : a.k <= 24 ? gather_d2<STORAGE, DP, 24>(src, nrow, a.k, qv)
                                                   : gather_d2<STORAGE, DP>(src, nrow, a.k, qv);
-                    unsigned um = __ballot_sync(FULL, valid && !seen);
-                    if (um == 0u) break;  // every neighbour visited: local maximum
-                    um = lowest_bits(um, limit - evals);
                     int mi;
                     unsigned evc;
                     if (a.climb == KNN_CLIMB_BEST) {
@@ -378,26 +392,35 @@ ignns_search_kernel(const SearchArgs a) {
                 if (cn > 0) {
                     aid = cid;
                     aj = cj;
+                    asame = csame;
                     an = cn;
                 } else {
-                    an = draw(cap(limit - evals), aid, aj);
+                    an = draw(cap(limit - evals), aid, aj, asame);
                     if (an == 0) break;
                 }
                 G.issue(src, lane < an ? aid : 0u, an);
                 ad2 = G.reduce(an, qv);
-                bn = limit - evals - an > 0 ? draw(cap(limit - evals - an), bid, bj) : 0;
+                bn = limit - evals - an > 0 ? draw(cap(limit - evals - an), bid, bj, bsame) : 0;
                 continue;
             }
             aid = bid;
             aj = bj;
+            asame = bsame;
             an = bn;
             ad2 = bd2;
             bid = cid;
             bj = cj;
+            bsame = csame;
             bn = cn;
         }
 
         // ---- results and counters
+        unsigned long long draws_used = jlast;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long o = shfl_u64_xor(draws_used, off);
+            draws_used = o > draws_used ? o : draws_used;
+        }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const int idx = t * 32 + lane;
@@ -426,6 +449,13 @@ ignns_search_kernel(const SearchArgs a) {
 
 template <int ST, int DPV, int T>
 static cudaError_t launch_search_t(const SearchArgs &a, cudaStream_t s) {
+    if (a.m <= 0) {
+        // nothing to search: resolve both kernels, which loads their code now
+        // (with lazy module loading) rather than inside the first search
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, ignns_search_kernel<ST, DPV, T, true>);
+        return e == cudaSuccess ? cudaFuncGetAttributes(&fa, ignns_search_kernel<ST, DPV, T, false>) : e;
+    }
     const int grid = (a.m * a.parts + SEARCH_WARPS - 1) / SEARCH_WARPS;
     const size_t smem = search_smem_bytes(a.vis_n);
     if (smem <= SEARCH_SMEM_VIS_MAX) {
@@ -445,7 +475,6 @@ static cudaError_t launch_search_t(const SearchArgs &a, cudaStream_t s) {
 
 #define KNN_DEFINE_SEARCH_LAUNCHER(NAME, ST)                                              \
     cudaError_t NAME(int dp, const SearchArgs &a, cudaStream_t s) {                       \
-        if (a.m <= 0) return cudaSuccess;                                                 \
         switch (dp) {                                                                     \
             KNN_SEARCH_CASE(ST, 16)                                                       \
             KNN_SEARCH_CASE(ST, 32)                                                       \
