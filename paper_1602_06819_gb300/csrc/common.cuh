@@ -351,6 +351,50 @@ struct RowGather {
     }
 };
 
+// The first chunk of every lane's share of up to 32 rows: the first G * 16
+// bytes of each row.  reduce() leaves in lane c the sum of row c's squared
+// differences over those elements, accumulated as RowGather accumulates them.
+// Every step of that sum adds a nonnegative value and FP32 rounding is
+// monotone, so the partial sum never exceeds the full squared distance
+// RowGather (or gather_d2) computes for the same row.
+template <int STORAGE, int DP>
+struct RowGatherHead {
+    using C = RowCfg<STORAGE, DP>;
+    static constexpr int P = 32 / C::RPP;
+    uint4 buf[P];
+    float scl[P];
+
+    // As RowGather::issue: every pass loads; lane 0's rid must be a valid row.
+    __device__ __forceinline__ void issue(const RowSource &src, uint32_t rid, int nrows) {
+        const int lane = threadIdx.x & 31;
+        const int gl = lane / C::G, gi = lane % C::G;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int c = p * C::RPP + gl;
+            const uint32_t row = __shfl_sync(FULL, rid, c < nrows ? (c & 31) : 0);
+            buf[p] = ld_nc_v4(reinterpret_cast<const uint4 *>(src.rows + (size_t)row * C::ROW_BYTES) + gi);
+            scl[p] = STORAGE == ST_FP8 ? __uint_as_float(ld_nc_u32(src.scale + row)) : 1.0f;
+        }
+    }
+
+    __device__ __forceinline__ float reduce(int nrows, const float (&qv)[C::QF]) const {
+        const int lane = threadIdx.x & 31;
+        float result = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            RowAcc<STORAGE> ra;
+            ra.add(buf[p], qv, scl[p]);
+            float acc = ra.total();
+#pragma unroll
+            for (int off = C::G / 2; off >= 1; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+            const int c = lane - p * C::RPP;
+            const float got = __shfl_sync(FULL, acc, ((lane % C::RPP) * C::G) & 31);
+            if (c >= 0 && c < C::RPP && lane < nrows) result = got;
+        }
+        return result;
+    }
+};
+
 // The row layout with passes for MAX_ROWS rows (rounded up to whole passes)
 // in flight.
 template <int STORAGE, int DP, int MAX_ROWS>

@@ -240,22 +240,53 @@ ignns_search_kernel(const SearchArgs a) {
         // Batch A is decided while the rows of the next batch B load, and the
         // ids of the batch after B (C) are drawn meanwhile: B's loads start
         // as soon as A is settled.
-        RowGather<STORAGE, DP> G;
+        //
+        // A restart's squared distance matters for three things only: the
+        // expansion test, the offer to the result list and, when it is kept,
+        // the climb.  B first loads the head of each row (its first G * 16
+        // bytes); the partial sum over it is a lower bound of the full sum
+        // (in FP32 as well: every step adds a nonnegative value, rounding is
+        // monotone).
+        // A row whose partial sum is at least hi2 fails the expansion test
+        // whatever the rest holds (hi2 only falls as s_max rises) and, above
+        // the result list's worst distance (which only falls too), cannot
+        // enter it: it is discarded as the full distance would discard it and
+        // its distance is recorded as +inf.  The other rows get their full
+        // distance, summed exactly as a full gather sums it, in a second
+        // round trip.  Every restart still counts as one similarity
+        // computation.
+        constexpr bool SETTLE = C::CPL >= 2;  // the head is shorter than the row
+        RowGatherHead<STORAGE, DP> H;
+        auto full_d2 = [&](uint32_t id, int n) -> float {  // lanes < n: rows id
+            return n <= 12 ? gather_d2<STORAGE, DP, 12>(src, lane < n ? id : 0u, n, qv)
+                           : gather_d2<STORAGE, DP>(src, lane < n ? id : 0u, n, qv);
+        };
+        auto settle = [&](float part, uint32_t id, int n) -> float {
+            if (!SETTLE) return part;  // the head was the whole row
+            const bool out = a.discard && part >= hi2 && part > key_d2(top.worst);
+            const unsigned need = __ballot_sync(FULL, lane < n && !out);
+            float d2 = out ? INF : part;
+            if (need) {
+                // the rows that need it, compacted to the first lanes
+                const int cnt = __popc(need);
+                const uint32_t nid = __shfl_sync(FULL, id, lane < cnt ? (int)__fns(need, 0, lane + 1) : 0);
+                const float f = full_d2(nid, cnt);
+                const float mine = __shfl_sync(FULL, f, __popc(need & lt_mask) & 31);
+                if ((need >> lane) & 1u) d2 = mine;
+            }
+            return d2;
+        };
         uint32_t aid = 0xffffffffu, bid = 0xffffffffu;
         uint64_t aj = 0, bj = 0;
         unsigned asame = 0u, bsame = 0u;
         int an = done ? 0 : draw(cap(limit), aid, aj, asame);
-        float ad2 = __int_as_float(0x7f800000);
-        if (an > 0) {
-            G.issue(src, lane < an ? aid : 0u, an);
-            ad2 = G.reduce(an, qv);
-        }
+        float ad2 = an > 0 ? full_d2(aid, an) : INF;
         int bn = an > 0 && limit - an > 0 ? draw(cap(limit - an), bid, bj, bsame) : 0;
         while (an > 0) {
             // ---- start B's loads, then draw C (filtered by the marks so far).
             // issue and reduce are paired unconditionally, so the row buffer
             // is visibly dead after the reduce
-            G.issue(src, lane < bn ? bid : 0u, bn);
+            H.issue(src, lane < bn ? bid : 0u, bn);
             uint32_t cid = 0xffffffffu;
             uint64_t cj = 0;
             unsigned csame = 0u;
@@ -302,7 +333,7 @@ ignns_search_kernel(const SearchArgs a) {
             int ai = segment(0);
             int32_t nbk = ai < 32 ? list_of(ai) : -1;
             // B's distances, before any climb (one row buffer is live at a time)
-            const float bd2 = G.reduce(bn, qv);
+            const float bd2 = settle(H.reduce(bn, qv), bid, bn);
 
             while (ai < 32) {
                 const float d2a = __shfl_sync(FULL, ad2, ai);
@@ -398,8 +429,7 @@ ignns_search_kernel(const SearchArgs a) {
                     an = draw(cap(limit - evals), aid, aj, asame);
                     if (an == 0) break;
                 }
-                G.issue(src, lane < an ? aid : 0u, an);
-                ad2 = G.reduce(an, qv);
+                ad2 = full_d2(aid, an);
                 bn = limit - evals - an > 0 ? draw(cap(limit - evals - an), bid, bj, bsame) : 0;
                 continue;
             }
