@@ -116,10 +116,15 @@ def exact_build_report(W, n, ms, info):
 
 
 def search_source_hash() -> str:
+    """Hash of the search kernel's code (comments and blank space removed, so
+    that editing a comment does not disown a capture of the same kernel)."""
     h = hashlib.sha256()
     for name in SEARCH_SOURCES:
-        with open(os.path.join(ROOT, "paper_1602_06819_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1602_06819_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

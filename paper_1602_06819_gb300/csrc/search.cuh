@@ -15,7 +15,8 @@
 //   state, so the warp draws batches of up to 32 unvisited candidates ahead
 //   and gathers a batch's rows together (16-byte coalesced loads, all in
 //   flight at once): while one batch is decided the next one loads and the
-//   one after it is drawn.
+//   one after it is drawn.  A restart's row is first read in part; most are
+//   settled by the partial sum, a lower bound (see the restart loop).
 //   Between two accepted restarts the search only counts, marks and offers:
 //   one ballot finds the first candidate the expansion test keeps, and every
 //   candidate before it is committed at once (a discarded restart cannot
@@ -246,15 +247,14 @@ ignns_search_kernel(const SearchArgs a) {
         // the climb.  B first loads the head of each row (its first G * 16
         // bytes); the partial sum over it is a lower bound of the full sum
         // (in FP32 as well: every step adds a nonnegative value, rounding is
-        // monotone).
-        // A row whose partial sum is at least hi2 fails the expansion test
-        // whatever the rest holds (hi2 only falls as s_max rises) and, above
-        // the result list's worst distance (which only falls too), cannot
-        // enter it: it is discarded as the full distance would discard it and
-        // its distance is recorded as +inf.  The other rows get their full
-        // distance, summed exactly as a full gather sums it, in a second
-        // round trip.  Every restart still counts as one similarity
-        // computation.
+        // monotone).  A row whose partial sum is at least hi2 fails the
+        // expansion test whatever the rest holds (hi2 only falls as s_max
+        // rises) and, above the result list's worst distance (which only
+        // falls too), cannot enter it: it is discarded as the full distance
+        // would discard it and its distance is recorded as +inf.  The other
+        // rows get their full distance, summed exactly as a full gather sums
+        // it, in a second round trip.  Every restart still counts as one
+        // similarity computation.
         constexpr bool SETTLE = C::CPL >= 2;  // the head is shorter than the row
         RowGatherHead<STORAGE, DP> H;
         auto full_d2 = [&](uint32_t id, int n) -> float {  // lanes < n: rows id
