@@ -299,64 +299,14 @@ struct RowAcc<ST_BF16> {
     __device__ __forceinline__ float total() const { return f32x2_total(a, b); }
 };
 
-// Row gathers split in two: issue() starts the loads of up to ROWS rows
-// (lane c < nrows holds row id rid) and reduce() waits for them, leaving the
-// squared distance of row c in lane c.  Work placed between the two calls
-// overlaps with the loads.
-template <int STORAGE, int DP>
-struct RowGather {
-    // at most 32 16-byte chunks per lane (128 registers) stay in flight
-    using C0 = RowCfg<STORAGE, DP>;
-    struct C : C0 {
-        static constexpr int P = C0::P * C0::CPL <= 32 ? C0::P : (32 / C0::CPL > 0 ? 32 / C0::CPL : 1);
-    };
-    static constexpr int ROWS = C::P * C::RPP < 32 ? C::P * C::RPP : 32;
-    uint4 buf[C::P][C::CPL];
-    float scl[C::P];
-
-    // Every pass loads (a group past the last row re-reads the row of lane
-    // 0, whose rid must be a valid row even for nrows = 0; the result is
-    // dropped), so that reduce() runs straight through and the arithmetic of
-    // the passes interleaves.
-    __device__ __forceinline__ void issue(const RowSource &src, uint32_t rid, int nrows) {
-        const int lane = threadIdx.x & 31;
-        const int gl = lane / C::G, gi = lane % C::G;
-#pragma unroll
-        for (int p = 0; p < C::P; ++p) {
-            const int c = p * C::RPP + gl;
-            const uint32_t row = __shfl_sync(FULL, rid, c < nrows ? (c & 31) : 0);
-            const uint4 *base = reinterpret_cast<const uint4 *>(src.rows + (size_t)row * C::ROW_BYTES);
-#pragma unroll
-            for (int k = 0; k < C::CPL; ++k) buf[p][k] = ld_nc_v4(base + gi + k * C::G);
-            scl[p] = STORAGE == ST_FP8 ? __uint_as_float(ld_nc_u32(src.scale + row)) : 1.0f;
-        }
-    }
-
-    __device__ __forceinline__ float reduce(int nrows, const float (&qv)[C::QF]) const {
-        const int lane = threadIdx.x & 31;
-        float result = __int_as_float(0x7f800000);
-#pragma unroll
-        for (int p = 0; p < C::P; ++p) {
-            RowAcc<STORAGE> ra;
-#pragma unroll
-            for (int k = 0; k < C::CPL; ++k) ra.add(buf[p][k], qv + k * C::E, scl[p]);
-            float acc = ra.total();
-#pragma unroll
-            for (int off = C::G / 2; off >= 1; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
-            const int c = lane - p * C::RPP;
-            const float got = __shfl_sync(FULL, acc, ((lane % C::RPP) * C::G) & 31);
-            if (c >= 0 && c < C::RPP && lane < nrows) result = got;
-        }
-        return result;
-    }
-};
-
-// The first chunk of every lane's share of up to 32 rows: the first G * 16
-// bytes of each row.  reduce() leaves in lane c the sum of row c's squared
-// differences over those elements, accumulated as RowGather accumulates them.
-// Every step of that sum adds a nonnegative value and FP32 rounding is
-// monotone, so the partial sum never exceeds the full squared distance
-// RowGather (or gather_d2) computes for the same row.
+// A row gather split in two: issue() starts the loads of the first chunk of
+// every lane's share of up to 32 rows (the first G * 16 bytes of each row;
+// lane c < nrows holds row id rid) and reduce() waits for them, leaving in
+// lane c the sum of row c's squared differences over those elements,
+// accumulated as gather_d2 starts its sum.  Work placed between the two calls
+// overlaps with the loads.  Every step of that sum adds a nonnegative value
+// and FP32 rounding is monotone, so the partial sum never exceeds the full
+// squared distance gather_d2 computes for the same row.
 template <int STORAGE, int DP>
 struct RowGatherHead {
     using C = RowCfg<STORAGE, DP>;
@@ -364,7 +314,10 @@ struct RowGatherHead {
     uint4 buf[P];
     float scl[P];
 
-    // As RowGather::issue: every pass loads; lane 0's rid must be a valid row.
+    // Every pass loads (a group past the last row re-reads the row of lane
+    // 0, whose rid must be a valid row even for nrows = 0; the result is
+    // dropped), so that reduce() runs straight through and the arithmetic of
+    // the passes interleaves.
     __device__ __forceinline__ void issue(const RowSource &src, uint32_t rid, int nrows) {
         const int lane = threadIdx.x & 31;
         const int gl = lane / C::G, gi = lane % C::G;

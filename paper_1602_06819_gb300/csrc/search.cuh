@@ -106,7 +106,7 @@ template <int STORAGE, int DP, int T, bool SMEM_VIS>
 __global__ void __launch_bounds__(SEARCH_WARPS * 32, 8 / SEARCH_WARPS)
 ignns_search_kernel(const SearchArgs a) {
     using C = RowCfg<STORAGE, DP>;
-    constexpr int NB = RowGather<STORAGE, DP>::ROWS;  // restart candidates per batch
+    constexpr int NB = 32;  // restart candidates per batch (one a lane)
     extern __shared__ uint32_t s_visited[];  // SMEM_VIS: one bitset per warp
     __shared__ uint32_t s_id[SEARCH_WARPS][32];
     __shared__ uint64_t s_j[SEARCH_WARPS][32];

@@ -152,6 +152,16 @@ def test_queries_d128_many_tiles(knn):
     compare(knn, X0, Q, 10, 10, 4.0, 5.0, seed=4, max_ambiguous=0.6)
 
 
+@pytest.mark.parametrize("d,storage", [(200, 0), (256, 1)])
+def test_queries_widest_rows(knn, d, storage):
+    """The widest rows (padded to 256): a restart's head is 128 bytes of a
+    1,024-byte (FP32) or 512-byte (BF16) row, so fewer restarts are settled
+    by their partial sums and more take the full second gather."""
+    mix = Mixture(d=d, components=10, half_width=20.0, sigma=1.0, seed=23)
+    X0, Q = mix.sample(2500, 1), mix.sample(48, 3)
+    compare(knn, X0, Q, 10, 10, 4.0, 5.0, seed=4, storage=storage, max_ambiguous=0.6)
+
+
 def test_queries_ragged_dims_and_k_out(knn):
     mix = Mixture(d=3, components=5, half_width=10.0, sigma=1.0, seed=2)
     X0, Q = mix.sample(700, 1), mix.sample(48, 3)
