@@ -76,6 +76,9 @@ struct knn_graph {
     unsigned long long *totals = nullptr;
     int64_t *out_ids_dev = nullptr;
     float *out_sims_dev = nullptr;
+    uint64_t *cross_keys = nullptr;      // best k of each new point among its batch [M][K]
+    cudaStream_t side = nullptr;         // the batch's own similarities run here beside the search
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t last_stream = nullptr;
     int64_t launches = 0;          // kernels launched by this library for the graph
     bool timing = false;           // record events around each phase
@@ -225,6 +228,9 @@ static void free_graph(knn_graph *g) {
     for (void *p : g->allocations) cudaFree(p);
     for (cudaEvent_t e : g->ev)
         if (e) cudaEventDestroy(e);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->side) cudaStreamDestroy(g->side);
     delete g;
 }
 
@@ -413,7 +419,7 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
                   (size_t)M * g->KT * 8 + (size_t)M * K * 8 + (size_t)M * NCTR * 8 +
                   (size_t)g->offer_cap * 16 + (size_t)M * K * 12 + (size_t)M * levels * 4 +
                   (size_t)M * g->KT * 8 + (size_t)M * NCTR * 8 + (size_t)(2 * KNN_MAX_PARTS + 1) * 8 +
-                  (size_t)M * 8;
+                  (size_t)M * 8 + (size_t)M * K * 8;
     if (p.storage == KNN_STORAGE_BF16) need += (size_t)C * DP * 2;
     if (p.storage == KNN_STORAGE_FP8_E4M3) need += (size_t)C * DP + (size_t)C * 4;
     size_t free_b = 0, total_b = 0;
@@ -456,7 +462,14 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
     ALLOC(totals, NTOT)
     ALLOC(out_ids_dev, M * K)
     ALLOC(out_sims_dev, M * K)
+    ALLOC(cross_keys, M * K)
 #undef ALLOC
+    if (st == KNN_OK && (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        st = fail(KNN_ERR_CUDA, "creating the graph's side stream failed");
+    }
     if (st != KNN_OK) {
         free_graph(g);
         return st;
@@ -578,22 +591,33 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     phase_mark(g, KNN_PHASE_STORE, s);
     TRY(append_rows(g, vecs, m, n0, g->X, true, s));
     g->phase_ran[KNN_PHASE_STORE] = true;
-    // a2-a5: iGNNS of every new point against the n0 nodes before the batch
-    phase_mark(g, KNN_PHASE_SEARCH, s);
-    const uint64_t *keys = nullptr;
-    TRY(run_search(g, g->X + n0 * g->dp, m, K, (uint64_t)n0, s, &keys));
-    phase_mark(g, KNN_PHASE_CROSS, s);
-    // a6: exact similarities among the batch, written as the new lists
+    // a6, first half: exact similarities among the batch (the best k of each
+    // new point) on the side stream, beside the search: they need only the
+    // stored rows, and SMs the search leaves free take them
     CrossArgs ca{};
     ca.rows = g->X;
-    ca.in_keys = keys;
+    ca.cross_keys = g->cross_keys;
     ca.nbr_ids = g->nbr_ids;
     ca.nbr_d2 = g->nbr_d2;
     ca.totals = g->totals;
     ca.m = (int32_t)m;
     ca.k = K;
     ca.n = (uint32_t)n0;
-    CU(launch_cross(g->dp, ca, s));
+    CU(cudaEventRecord(g->ev_fork, s));
+    CU(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+    CU(launch_cross_topk(g->dp, ca, g->side));
+    CU(cudaEventRecord(g->ev_join, g->side));
+    ++g->launches;
+    // a2-a5: iGNNS of every new point against the n0 nodes before the batch
+    phase_mark(g, KNN_PHASE_SEARCH, s);
+    const uint64_t *keys = nullptr;
+    TRY(run_search(g, g->X + n0 * g->dp, m, K, (uint64_t)n0, s, &keys));
+    phase_mark(g, KNN_PHASE_CROSS, s);
+    // a6, second half: each new list is the best k of the search result and
+    // of the batch
+    ca.in_keys = keys;
+    CU(cudaStreamWaitEvent(s, g->ev_join, 0));
+    CU(launch_cross_merge(ca, s));
     ++g->launches;
     g->phase_ran[KNN_PHASE_CROSS] = true;
     // a7-a8: Update (Algorithm 2): collect candidates, then merge them

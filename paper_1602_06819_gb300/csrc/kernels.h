@@ -110,6 +110,7 @@ struct RescoreArgs {
 struct CrossArgs {
     const float *rows;           // FP32 padded rows; the batch is rows n .. n+m-1
     const uint64_t *in_keys;     // [m][k] search result of each new point
+    uint64_t *cross_keys;        // [m][k] best k among the batch (split form)
     int32_t *nbr_ids;            // lists; rows n .. n+m-1 are written
     float *nbr_d2;
     unsigned long long *totals;
@@ -186,6 +187,10 @@ cudaError_t launch_search(int storage, int dp, const SearchArgs &a, cudaStream_t
 bool search_visited_on_chip(uint32_t n);
 cudaError_t launch_rescore(int dp, const RescoreArgs &a, cudaStream_t s);
 cudaError_t launch_cross(int dp, const CrossArgs &a, cudaStream_t s);
+// the same lists in two launches (a single graph): the best k among the batch
+// into cross_keys (needs no search result), then the merge with in_keys
+cudaError_t launch_cross_topk(int dp, const CrossArgs &a, cudaStream_t s);
+cudaError_t launch_cross_merge(const CrossArgs &a, cudaStream_t s);
 cudaError_t launch_update(int dp, const UpdateArgs &a, cudaStream_t s);
 cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t s);
 // true when Update keeps its seen bitsets (seen_words words each) on chip

@@ -69,9 +69,17 @@ __global__ void __launch_bounds__(UPD_WARPS * 32) rescore_kernel(const RescoreAr
 }
 
 // ---------------------------------------------------------------------------
-// Cross-merge among the points of one batch.
+// Cross-merge among the points of one batch.  FUSED: the list of new point i
+// is the best k of its search result and of the other points of its batch.
+// Split in two for a single graph: cross_topk keeps the best k among the
+// batch (it needs no search result and runs beside the search) and
+// cross_merge then takes the best k of the two lists.  Keys are unique (a
+// search finds old nodes, the batch holds new ones), so both give the same
+// list: the best k of a union are the best k of the two lists' best k.
 // ---------------------------------------------------------------------------
-template <int DP>
+enum { CROSS_FUSED = 0, CROSS_TOPK = 1 };
+
+template <int DP, int MODE>
 __device__ __forceinline__ void cross_item(const CrossArgs &a, int i, int lane) {
     using C = RowCfg<ST_FP32, DP>;
     // the new point's id and the batch points it meets: those of its graph
@@ -89,8 +97,10 @@ __device__ __forceinline__ void cross_item(const CrossArgs &a, int i, int lane) 
     const RowSource src{reinterpret_cast<const uint8_t *>(a.rows), nullptr};
     WarpTop<1> top;
     top.init(a.k);
-    top.e[0] = lane < a.k ? a.in_keys[(size_t)i * a.k + lane] : KEY_EMPTY;
-    top.worst = top.entry(a.k - 1);
+    if (MODE == CROSS_FUSED) {
+        top.e[0] = lane < a.k ? a.in_keys[(size_t)i * a.k + lane] : KEY_EMPTY;
+        top.worst = top.entry(a.k - 1);
+    }
     for (int j0 = j_lo; j0 < j_hi; j0 += 32) {
         const int nr = j_hi - j0 < 32 ? j_hi - j0 : 32;
         const uint32_t id = id0 + (uint32_t)(j0 - j_lo + lane);
@@ -100,7 +110,9 @@ __device__ __forceinline__ void cross_item(const CrossArgs &a, int i, int lane) 
             top.offer(pack_key(__shfl_sync(FULL, d2, t), id0 + (uint32_t)(j0 - j_lo + t)));
         }
     }
-    if (lane < a.k) {
+    if (MODE == CROSS_TOPK) {
+        if (lane < a.k) a.cross_keys[(size_t)i * a.k + lane] = top.e[0];
+    } else if (lane < a.k) {
         const uint64_t key = top.e[0];
         a.nbr_ids[(size_t)new_id * a.k + lane] = key == KEY_EMPTY ? -1 : (int32_t)key_id(key);
         a.nbr_d2[(size_t)new_id * a.k + lane] = key == KEY_EMPTY ? __int_as_float(0x7f800000) : key_d2(key);
@@ -108,12 +120,35 @@ __device__ __forceinline__ void cross_item(const CrossArgs &a, int i, int lane) 
     if (lane == 0 && j_hi - j_lo > 1) atomicAdd(a.totals + TOT_CROSS_EVALS, (unsigned long long)(j_hi - j_lo - 1));
 }
 
-template <int DP>
+template <int DP, int MODE>
 __global__ void __launch_bounds__(UPD_WARPS * 32) cross_kernel(const CrossArgs a) {
     const int lane = threadIdx.x & 31;
     const int m = a.seg.count ? *a.seg.count : a.m;
     for (int i = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5); i < m; i += gridDim.x * UPD_WARPS)
-        cross_item<DP>(a, i, lane);
+        cross_item<DP, MODE>(a, i, lane);
+}
+
+// The list of new point i: the best k of its search result (in_keys) and of
+// its best k among the batch (cross_keys); a single graph only.
+__global__ void __launch_bounds__(UPD_WARPS * 32) cross_merge_kernel(const CrossArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5);
+    if (i >= a.m) return;  // warp-uniform
+    WarpTop<1> top;
+    top.init(a.k);
+    top.e[0] = lane < a.k ? a.in_keys[(size_t)i * a.k + lane] : KEY_EMPTY;
+    top.worst = top.entry(a.k - 1);
+    const uint64_t ck = lane < a.k ? a.cross_keys[(size_t)i * a.k + lane] : KEY_EMPTY;
+    for (int t = 0; t < a.k; ++t) {
+        const uint64_t key = shfl_u64(ck, t);
+        if (key == KEY_EMPTY || !top.offer(key)) break;  // the batch list is sorted
+    }
+    const uint32_t new_id = a.n + (uint32_t)i;
+    if (lane < a.k) {
+        const uint64_t key = top.e[0];
+        a.nbr_ids[(size_t)new_id * a.k + lane] = key == KEY_EMPTY ? -1 : (int32_t)key_id(key);
+        a.nbr_d2[(size_t)new_id * a.k + lane] = key == KEY_EMPTY ? __int_as_float(0x7f800000) : key_d2(key);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -345,7 +380,7 @@ static cudaError_t rescore_dp(const RescoreArgs &a, cudaStream_t s) {
 }
 template <int DP>
 static cudaError_t cross_dp(const CrossArgs &a, cudaStream_t s) {
-    cross_kernel<DP><<<(a.m + UPD_WARPS - 1) / UPD_WARPS, UPD_WARPS * 32, 0, s>>>(a);
+    cross_kernel<DP, CROSS_FUSED><<<(a.m + UPD_WARPS - 1) / UPD_WARPS, UPD_WARPS * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <int DP>
@@ -382,6 +417,23 @@ cudaError_t launch_rescore(int dp, const RescoreArgs &a, cudaStream_t s) {
 cudaError_t launch_cross(int dp, const CrossArgs &a, cudaStream_t s) {
     if (a.m <= 0) return cudaSuccess;
     KNN_DP_DISPATCH(cross_dp, dp, a, s)
+}
+
+template <int DP>
+static cudaError_t cross_topk_dp(const CrossArgs &a, cudaStream_t s) {
+    cross_kernel<DP, CROSS_TOPK><<<(a.m + UPD_WARPS - 1) / UPD_WARPS, UPD_WARPS * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cross_topk(int dp, const CrossArgs &a, cudaStream_t s) {
+    if (a.m <= 0) return cudaSuccess;
+    KNN_DP_DISPATCH(cross_topk_dp, dp, a, s)
+}
+
+cudaError_t launch_cross_merge(const CrossArgs &a, cudaStream_t s) {
+    if (a.m <= 0) return cudaSuccess;
+    cross_merge_kernel<<<(a.m + UPD_WARPS - 1) / UPD_WARPS, UPD_WARPS * 32, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_update(int dp, const UpdateArgs &a, cudaStream_t s) {
