@@ -67,6 +67,8 @@ def parse_args():
                          "iGNNS against GNNS at equal evaluations) or the DEPTH sweep, "
                          "one JSON line per point")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the precision record (BF16 / FP8 / FP32 searches at 1,000,000 x 96)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
@@ -225,14 +227,46 @@ def quality_q(e_c, n, n_a, k):
 # the CPU oracle, timed (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample_setup(W, n_sample=20000):
-    """Untimed setup of the oracle sample: the exact graph of the first
-    n_sample points of the initial set, built by the oracle itself."""
+ORACLE_MAX_INIT = 100_000
+
+
+def oracle_initial_graph(W):
+    """Untimed setup of the oracle's timed samples: the oracle's exact graph
+    (Sec. 2.1) of the workload's initial points (at most the first 100,000:
+    the 1,000,000-point workload's would take hours), built on every host
+    core.  The lists are kept in the temp directory, keyed by the points and
+    the oracle library, so the other arm of the same run on this machine
+    reuses them; returns (graph, build seconds, whether it was reused)."""
+    import tempfile
+
+    import numpy as np
     import oracle
-    oracle.build()
-    X0 = W.initial()[:n_sample]
-    g = oracle.Graph.exact(X0, W.k, capacity=n_sample + 40000)
-    return g
+    lib = oracle.build()
+    n0 = min(W.n_init, ORACLE_MAX_INIT)
+    X0 = W.initial()[:n0]
+    h = hashlib.sha256(X0.tobytes())
+    with open(lib, "rb") as f:
+        h.update(f.read())
+    path = os.path.join(tempfile.gettempdir(), f"knn_oracle_exact_{W.name}_{h.hexdigest()[:16]}.npz")
+    t0 = time.perf_counter()
+    reused = False
+    try:
+        z = np.load(path)
+        ids, sims = z["ids"], z["sims"]
+        reused = ids.shape == (n0, W.k)
+    except Exception:
+        pass
+    if not reused:
+        ids, sims, _ = oracle.exact_knn(X0, W.k)
+        tmp = path + f".{os.getpid()}.npz"
+        np.savez(tmp, ids=ids, sims=sims)
+        os.replace(tmp, path)
+    g = oracle.Graph(W.mixture.d, W.k, n0 + min(W.n_insert, 20_000))
+    g.X[:n0] = X0
+    g.ids[:n0] = ids
+    g.sims[:n0] = sims
+    g.n = n0
+    return g, time.perf_counter() - t0, reused
 
 
 def oracle_cores() -> int:
@@ -240,28 +274,30 @@ def oracle_cores() -> int:
 
 
 def run_cpu_baseline(args, W, n_full_avg):
-    """Sequential oracle (Algorithm 1, FP64) on a prefix of the workload."""
-    g = oracle_sample_setup(W)
-    Xs = W.stream(40000)
+    """Sequential oracle (Algorithm 1, FP64) on the first points of the
+    benchmark's own stream, inserted into the oracle's exact graph of the
+    initial points: the same workload at the n the GPU run starts from."""
+    g, setup_s, reused = oracle_initial_graph(W)
+    Xs = W.stream()
     n_start = g.n
     done, t0 = 0, time.perf_counter()
-    while done < 32768 and time.perf_counter() - t0 < args.cpu_seconds:
-        g.insert_stream(Xs[done:done + 256], args.speedup, args.expansion, args.depth,
+    while done < 16384 and done + 64 <= g.capacity - n_start and \
+            time.perf_counter() - t0 < args.cpu_seconds:
+        g.insert_stream(Xs[done:done + 64], args.speedup, args.expansion, args.depth,
                         W.seed_search)
-        done += 256
+        done += 64
     dt = time.perf_counter() - t0
     rate = done / dt
-    n_avg = n_start + done / 2
     return {
-        "value": rate * n_avg / n_full_avg, "unit": UNIT, "cores": oracle_cores(),
-        "kind": "oracle",
-        "sample": (f"FP64 oracle, Algorithm 1 one point at a time on 1 thread: {done} stream "
-                   f"points into the exact graph of the first {n_start} initial points "
-                   f"(speedup {args.speedup:g}, e {args.expansion:g}, DEPTH {args.depth}) in "
-                   f"{dt:.1f} s = {rate:.1f} inserts/s at mean n {n_avg:.0f}; scaled by "
-                   f"{n_avg:.0f}/{n_full_avg:.0f} (the iGNNS cost of an insert is "
-                   f"n/speedup similarities) to the timed GPU region's mean n"),
-        "measured_inserts_per_s": rate,
+        "value": rate, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+        "sample": (f"FP64 oracle, Algorithm 1 one point at a time on 1 thread: the first {done} "
+                   f"points of this stream inserted into the oracle's exact graph of the "
+                   f"{'' if n_start == W.n_init else 'first '}{n_start:,} initial points "
+                   f"(n {n_start:,} to {n_start + done:,}; the GPU's "
+                   f"timed batches run at mean n {n_full_avg:,.0f}), speedup {args.speedup:g}, "
+                   f"e {args.expansion:g}, DEPTH {args.depth}, in {dt:.1f} s; not scaled.  "
+                   f"Untimed setup: the oracle's exact initial graph on {os.cpu_count()} host "
+                   f"cores, {setup_s:.0f} s{' (reused from this run)' if reused else ''}"),
     }
 
 
@@ -270,9 +306,11 @@ def run_reference(args, W):
     if rank != 0:
         return
     n_full_avg = W.n_init + (args.warmup + args.steps / 2) * W.batch
-    g = oracle_sample_setup(W)
-    Xs = W.stream(40000)
+    g, setup_s, reused = oracle_initial_graph(W)
+    Xs = W.stream()
     per_step = 64
+    if (args.warmup + args.steps) * per_step > g.capacity - g.n:
+        per_step = max(1, (g.capacity - g.n) // (args.warmup + args.steps))
     pos = 0
     for _ in range(args.warmup):
         g.insert_stream(Xs[pos:pos + per_step], args.speedup, args.expansion, args.depth,
@@ -287,14 +325,14 @@ def run_reference(args, W):
         step_s.append(time.perf_counter() - t0)
         pos += per_step
     total = sum(step_s)
-    rate = args.steps * per_step / total
-    n_avg = n_start + args.steps * per_step / 2
-    value = rate * n_avg / n_full_avg
-    sample = (f"FP64 oracle, Algorithm 1 on 1 thread: each step inserts {per_step} stream "
-              f"points one at a time into the oracle's own graph (exact graph of the first "
-              f"{n_start - args.warmup * per_step} initial points, then the inserts so far); "
-              f"{rate:.1f} inserts/s at mean n {n_avg:.0f}, scaled by n/speedup to the GPU "
-              f"run's mean n {n_full_avg:.0f}")
+    value = args.steps * per_step / total
+    sample = (f"FP64 oracle, Algorithm 1 on 1 thread: each step inserts the next {per_step} points "
+              f"of this stream one at a time into the oracle's graph (its exact graph of the "
+              f"{'' if g.n - pos == W.n_init else 'first '}{g.n - pos:,} initial points, then "
+              f"the inserts so far; n {n_start:,} to {g.n:,}; "
+              f"the GPU's timed batches run at mean n {n_full_avg:,.0f}); not scaled.  Untimed "
+              f"setup: the exact initial graph on {os.cpu_count()} host cores, {setup_s:.0f} s"
+              f"{' (reused from this run)' if reused else ''}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup,
@@ -334,6 +372,152 @@ def workload_config(args, W):
 
 def kmedoids_clusters(n):
     return max(1, min(1024, n // 1000))
+
+
+SEQ_RECALL = os.path.join(ROOT, "tests", "golden", "sequential_recall_d128.txt")
+
+
+def sequential_oracle_recall(args, W, inserts):
+    """Graph quality the sequential build (Algorithm 1, FP64 oracle) reaches
+    on this stream after the same number of inserts: a stored value, written
+    by tests/golden/make_sequential_recall.py from the oracle alone, for the
+    d = 128 workload at its default parameters (speedup 4, e 5, DEPTH 2)."""
+    from paper_1602_06819_gb300 import inputs
+    if (W is not inputs.PLAIN_D128 or (args.speedup, args.expansion, args.depth) != (4.0, 5.0, 2)
+            or args.storage != "fp32" or args.order != "none"):
+        return None
+    try:
+        with open(SEQ_RECALL) as f:
+            rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    for r in rows:
+        if int(r[0]) == inserts:
+            return {"edge_recall": float(r[4]), "inserted_recall": float(r[5]), "Q": float(r[6]),
+                    "search_evals_per_insert": float(r[7]),
+                    "update_evals_per_insert": float(r[8]),
+                    "source": os.path.relpath(SEQ_RECALL, ROOT)}
+    return None
+
+
+def recall_record(recall, recall_new, q, n_final, seq):
+    """Edge recall (Sec. 8.5's correct edges over n*k) of the final graph and
+    of the inserted points' lists alone, beside the sequential oracle's on
+    the same stream (batches are held to it within 0.01)."""
+    rec = {"edge_recall": recall, "inserted_recall": recall_new, "target": RECALL_TARGET,
+           "target_met": recall >= RECALL_TARGET, "Q": q, "n_final": n_final,
+           "oracle_sequential": seq}
+    if seq is not None:
+        d_all = recall - seq["edge_recall"]
+        d_new = recall_new - seq["inserted_recall"]
+        rec["delta_vs_oracle"] = {"edge_recall": d_all, "inserted_recall": d_new,
+                                  "bound": 0.01,
+                                  "within": abs(d_all) <= 0.01 and abs(d_new) <= 0.01}
+    return rec
+
+
+def run_precision_record(knn, torch, np, hbm_peak, peak_src, steps=20, warmup=3):
+    """The precision workload (1,000,000 initial points, d = 96, 1,000
+    components, k = 20), one graph per searched copy: FP32, BF16 and
+    FP8-E4M3 screening with an FP32 re-score of the best 4k candidates.  Per
+    form: 1,024-point insert batches timed as the main line times them (L2
+    flushed between steps), the search kernel's roofline, the edge recall of
+    the inserted points' lists against the exact graph, and the similarity
+    error against FP64 (numpy, on sampled pairs): of the lists' FP32
+    similarities, and of the screening copy's similarities."""
+    from paper_1602_06819_gb300 import inputs
+    W = inputs.PRECISION_D96
+    n0, B, k, d = W.n_init, W.batch, W.k, W.mixture.d
+    X0h = W.initial()
+    Xsh = W.mixture.sample((steps + warmup) * B, W.seed_stream)
+    X0, Xs = torch.from_numpy(X0h).cuda(), torch.from_numpy(Xsh).cuda()
+    n_final = n0 + (steps + warmup) * B
+    exact = torch.empty((n_final - n0, k), dtype=torch.int64, device="cuda")
+    full = torch.empty((n_final, k), dtype=torch.int64, device="cuda")
+    knn.knn_exact_graph(torch.cat([X0, Xs]), k, full)
+    exact.copy_(full[n0:])
+    del full
+    rng = np.random.default_rng(7)
+    Xcat = np.vstack([X0h, Xsh])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = []
+    for storage in ("fp32", "bf16", "fp8"):
+        st = {"fp32": knn.KNN_STORAGE_FP32, "bf16": knn.KNN_STORAGE_BF16,
+              "fp8": knn.KNN_STORAGE_FP8_E4M3}[storage]
+        cfg = knn.GraphConfig(dim=d, k=k, depth=2, storage=st, speedup=4.0, expansion=W.expansion,
+                              rescore_mult=4, max_batch=B, seed=W.seed_search, capacity=n_final)
+        g = knn.Graph(cfg, X0)
+        g.set_timing(True)
+        for i in range(warmup):
+            g.insert(Xs[i * B:(i + 1) * B])
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        search_ms = 0.0
+        torch.cuda.synchronize()
+        st0 = g.stats()
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = ev[i]
+            a.record()
+            g.insert(Xs[(warmup + i) * B:(warmup + i + 1) * B])
+            b.record()
+            search_ms += g.last_timing()["search"]
+        torch.cuda.synchronize()
+        st1 = g.stats()
+        step_ms = sum(a.elapsed_time(b) for a, b in ev)
+        ids = torch.empty((n_final, k), dtype=torch.int64, device="cuda")
+        sims = torch.empty((n_final, k), dtype=torch.float32, device="cuda")
+        g.edges(ids, sims)
+        g.close()
+        new_ids = ids[n0:]
+        recall_new = edge_recall(torch, new_ids, exact) / exact.numel()
+        # similarity error against FP64 on sampled (node, neighbour) pairs
+        rows = rng.choice(n_final, 2048, replace=False)
+        cols = rng.integers(0, k, 2048)
+        ih, sh = ids.cpu().numpy(), sims.cpu().numpy()
+        nb = ih[rows, cols]
+        xa, xb = Xcat[rows].astype(np.float64), Xcat[nb].astype(np.float64)
+        s64 = 1.0 / (1.0 + np.linalg.norm(xa - xb, axis=1))
+        list_err = np.abs(sh[rows, cols] - s64) / s64
+        # the screening similarity: the stored copy of the neighbour's row
+        # against the node's FP32 row, in FP64
+        Xf = torch.from_numpy(Xcat[nb])
+        if storage == "fp32":
+            scr = xb
+        elif storage == "bf16":
+            scr = Xf.bfloat16().double().numpy()
+        else:
+            scale = Xf.abs().amax(dim=1, keepdim=True).clamp_min(1e-30) / 448.0
+            scr = ((Xf / scale).to(torch.float8_e4m3fn).float() * scale).double().numpy()
+        s_scr = 1.0 / (1.0 + np.linalg.norm(xa - scr, axis=1))
+        scr_err = np.abs(s_scr - s64) / s64
+        del ids, sims, new_ids
+        dp = 96
+        row_bytes = {"fp32": 4 * dp, "bf16": 2 * dp, "fp8": dp + 4}[storage]
+        d_evals = st1["search_evals"] - st0["search_evals"]
+        d_adj = st1["adjacency_reads"] - st0["adjacency_reads"]
+        alg = (d_evals * row_bytes + d_adj * k * 4 + steps * B * 4 * dp) / steps
+        launch_ms = search_ms / steps
+        achieved = alg / (launch_ms / 1e3) / 1e9
+        out.append({
+            "storage": storage, "workload": W.name, "n_init": n0, "d": d, "k": k,
+            "inserts_per_s": steps * B / (step_ms / 1e3), "ms_per_step": step_ms / steps,
+            "search_ms_per_step": launch_ms,
+            "inserted_recall": recall_new,
+            "evals_per_insert": d_evals / (steps * B),
+            "similarity_rel_err_vs_fp64": {
+                "lists_max": float(list_err.max()), "lists_median": float(np.median(list_err)),
+                "screening_max": float(scr_err.max()),
+                "screening_median": float(np.median(scr_err)), "pairs": 2048},
+            "roofline": {"kernel": f"ignns_search_kernel<{storage},{dp}>", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "peak_source": f"{peak_src} hbm_gbs",
+                         "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms},
+            "steps": steps, "warmup": warmup,
+            "l2": "flushed between timed steps (256 MiB write)"})
+    del flush, X0, Xs, exact
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -697,7 +881,8 @@ def main():
         torch.cuda.synchronize()
         order_ms = o0.elapsed_time(o1)
         X0 = X0[perm].contiguous()
-    Xs_host = W.mixture.sample(n_stream, W.seed_stream + 1000 * rank)
+    # one fixed stream per rank; a run inserts its prefix
+    Xs_host = W.mixture.sample(max(n_stream, W.n_insert), W.seed_stream + 1000 * rank)[:n_stream]
     Xs = torch.from_numpy(Xs_host).cuda()
     capacity = W.n_init + n_stream
     storage = {"fp32": knn.KNN_STORAGE_FP32, "bf16": knn.KNN_STORAGE_BF16,
@@ -763,9 +948,12 @@ def main():
     online = torch.empty((n_final, W.k), dtype=torch.int64, device="cuda")
     g.edges(online)
     e_c = edge_recall(torch, online, exact)
+    e_c_new = edge_recall(torch, online[W.n_init:], exact[W.n_init:])
     recall = e_c / exact.numel()
+    recall_new = e_c_new / ((n_final - W.n_init) * W.k)
     q = quality_q(e_c, W.n_init, n_final - W.n_init, W.k)
     del exact, online, Xall
+    seq = sequential_oracle_recall(args, W, n_final - W.n_init) if rank == 0 else None
 
     # roofline of the dominant kernel (the iGNNS search)
     dp = next(v for v in (16, 32, 64, 96, 128, 256) if W.mixture.d <= v)
@@ -794,16 +982,27 @@ def main():
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        t0 = time.perf_counter()
+        e2e_s = 0.0
         for i in range(K):
+            # the same L2 flush as the device-timed steps, outside the clock
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             g2.insert(Xp[(Wm + i) * B:(Wm + i + 1) * B], ids_h, nbrs_h)
-        torch.cuda.synchronize()
-        wall_ms, _ = aggregate_replicas(dist, 1e3 * (time.perf_counter() - t0), K * B, device="cuda")
+            torch.cuda.synchronize()
+            e2e_s += time.perf_counter() - t0
+        wall_ms, _ = aggregate_replicas(dist, 1e3 * e2e_s, K * B, device="cuda")
         wall = wall_ms / 1e3
         g2.close()
         e2e = {"value": inserts / wall, "unit": UNIT,
                "h2d_bytes_per_step": B * W.mixture.d * 4,
                "d2h_bytes_per_step": B * W.k * 8}
+
+    precision = None
+    if rank == 0 and world == 1 and args.workload == "plain" and not args.no_precision:
+        del flush
+        torch.cuda.empty_cache()
+        precision = run_precision_record(knn, torch, np, peak, peak_src)
 
     cpu = None
     n_full_avg = n_before + K * B / 2
@@ -818,8 +1017,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[args.storage],
             "data": "synthetic", "config": workload_config(args, W),
-            "recall": {"edge_recall": recall, "target": RECALL_TARGET,
-                       "target_met": recall >= RECALL_TARGET, "Q": q, "n_final": n_final},
+            "recall": recall_record(recall, recall_new, q, n_final, seq),
             "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                            "unit": f"one {B:,}-point insert batch"},
             "evals_per_insert": {"search": d_evals / (K * B),
@@ -836,6 +1034,7 @@ def main():
                          "algorithmic_bytes_per_launch": alg_bytes_launch,
                          "launch_ms": search_ms},
             "e2e": e2e,
+            "precision": precision,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,

@@ -103,7 +103,10 @@ typedef enum knn_phase {
     KNN_PHASE_STORE = 0,   /* copy in, pad and encode the new rows           */
     KNN_PHASE_SEARCH = 1,  /* iGNNS (Sec. 3), visited sets cleared first      */
     KNN_PHASE_RESCORE = 2, /* FP32 re-score of screening candidates           */
-    KNN_PHASE_CROSS = 3,   /* similarities among the points of the batch      */
+    KNN_PHASE_CROSS = 3,   /* similarities among the points of the batch; in
+                              a single graph their top-k runs on a side stream
+                              beside the search, so this phase times only the
+                              merge with the search results              */
     KNN_PHASE_OFFERS = 4,  /* Update levels 1..DEPTH: candidates per node      */
     KNN_PHASE_MERGE = 5,   /* Update: merge candidates into the lists          */
     KNN_NUM_PHASES = 6
@@ -326,17 +329,23 @@ KNN_API knn_status knn_exact_set_wait_limit(int64_t ns);
  *
  * rows: [n, dim] float32; dim must be 16, 32, 64, 96, 128 or 256 (rows are
  * used as they are, without padding).  nbr_ids: [n, k] int32 lists, best
- * first, -1 for an empty slot.  queries: [m, dim] float32.  out_ids:
- * [m, k_out] int64; out_sims (nullable): [m, k_out] float32.  Every buffer
- * must be device memory of the current device; nothing is staged.  Query i
- * uses restart stream 2^63 + query_id0 + i and budget
+ * first, -1 for an empty slot; an entry outside 0..n-1 is treated as an
+ * empty slot (never followed, never read as a row).  queries: [m, dim]
+ * float32.  out_ids: [m, k_out] int64; out_sims (nullable): [m, k_out]
+ * float32.  Every buffer must be device memory of the current device
+ * (nothing is staged); rows and queries must start on a 16-byte boundary
+ * (they are read with 16-byte loads) and the other buffers on a multiple of
+ * their element size: anything else returns KNN_ERR_INVALID_ARG before any
+ * device work.  Query i uses restart stream 2^63 + query_id0 + i and budget
  * max(1, floor(n / speedup)), so it returns exactly what
  * knn_graph_query_batch returns for the same graph and query id.
  *
  * Temporaries live in a 16 MiB array inside the library (every GPU that
- * loads the library keeps it until the process exits); a call needs about
- * m * n / 8 bytes of it plus small per-query parts and returns
- * KNN_ERR_CAPACITY, before any device work, when that exceeds 16 MiB.  The
+ * loads the library keeps it until the process exits).  A call needs
+ * m * (8 * k_out + 64) + n / 8 bytes of it, rounded up per part, and, once
+ * n exceeds 225,280 (the visited sets of a block's queries no longer fit in
+ * shared memory), about m * n / 8 bytes more; it returns KNN_ERR_CAPACITY,
+ * before any device work, when that exceeds 16 MiB.  The
  * first call on a device looks up the array's device address (make that
  * first call before any stream capture).  All calls share the array: calls
  * that overlap on the GPU race; order them on one stream.  Returns after

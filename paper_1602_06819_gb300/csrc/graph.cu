@@ -611,7 +611,13 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     // a2-a5: iGNNS of every new point against the n0 nodes before the batch
     phase_mark(g, KNN_PHASE_SEARCH, s);
     const uint64_t *keys = nullptr;
-    TRY(run_search(g, g->X + n0 * g->dp, m, K, (uint64_t)n0, s, &keys));
+    knn_status sst = run_search(g, g->X + n0 * g->dp, m, K, (uint64_t)n0, s, &keys);
+    if (sst != KNN_OK) {
+        // the side stream's kernel may still write cross_keys: order it
+        // before anything the caller enqueues next on s
+        cudaStreamWaitEvent(s, g->ev_join, 0);
+        return sst;
+    }
     phase_mark(g, KNN_PHASE_CROSS, s);
     // a6, second half: each new list is the best k of the search result and
     // of the batch

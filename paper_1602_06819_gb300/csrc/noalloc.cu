@@ -19,6 +19,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -39,14 +40,19 @@ void *g_scratch_addr[kMaxDevices] = {};
 
 size_t round_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-bool on_device(const void *p) {
+// Device (or managed) memory of `device`: another GPU's memory would be read
+// over the interconnect, or fault, so it is refused like host memory.
+bool on_device(const void *p, int device) {
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    return (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) &&
+           attr.device == device;
 }
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 knn_status reject(knn_status st, const char *fmt, ...) {
     char buf[400];
@@ -92,29 +98,41 @@ extern "C" KNN_API knn_status knn_search_noalloc(const float *rows, int64_t n, i
     if (m < 1 || m > INT32_MAX) return reject(KNN_ERR_INVALID_ARG, "m must be >= 1");
     if (!(speedup > 0.0) || !std::isfinite(speedup)) return reject(KNN_ERR_INVALID_ARG, "bad speedup");
     if (std::isnan(expansion)) return reject(KNN_ERR_INVALID_ARG, "expansion is NaN");
-    if (!on_device(rows) || !on_device(nbr_ids) || !on_device(queries) || !on_device(out_ids) ||
-        (out_sims && !on_device(out_sims)))
-        return reject(KNN_ERR_INVALID_ARG, "every buffer must be device memory (nothing is staged)");
-
-    // scratch layout: result keys, counters, totals, removal bits, visited sets
-    const size_t words = (size_t)((n + 31) / 32);
-    const size_t off_keys = 0;
-    const size_t off_ctr = off_keys + round_up((size_t)m * k_out * sizeof(uint64_t));
-    const size_t off_tot = off_ctr + round_up((size_t)m * NCTR * sizeof(long long));
-    const size_t off_rem = off_tot + round_up(NTOT * sizeof(unsigned long long));
-    const size_t off_vis = off_rem + round_up(words * sizeof(uint32_t));
-    const size_t need = off_vis + round_up((size_t)m * words * sizeof(uint32_t));
-    if (need > kScratchBytes)
-        return reject(KNN_ERR_CAPACITY,
-                      "m = %lld queries over n = %lld nodes need %zu bytes of scratch; the fixed "
-                      "array holds %zu (about m * n / 8 bytes are needed): use fewer queries per call",
-                      (long long)m, (long long)n, need, kScratchBytes);
-
+    // rows and queries are read with 16-byte vector loads, lists and outputs
+    // with loads and stores of their element size (checked before any CUDA
+    // call: a misaligned vector load would fault the kernel)
+    if (!aligned(rows, 16) || !aligned(queries, 16))
+        return reject(KNN_ERR_INVALID_ARG, "rows and queries must start on a 16-byte boundary");
+    if (!aligned(nbr_ids, 4) || !aligned(out_ids, 8) || (out_sims && !aligned(out_sims, 4)))
+        return reject(KNN_ERR_INVALID_ARG, "nbr_ids, out_ids and out_sims must be aligned to "
+                                           "their element size");
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) {
         cudaGetLastError();
         return reject(KNN_ERR_CUDA, "no CUDA device");
     }
+    if (!on_device(rows, device) || !on_device(nbr_ids, device) || !on_device(queries, device) ||
+        !on_device(out_ids, device) || (out_sims && !on_device(out_sims, device)))
+        return reject(KNN_ERR_INVALID_ARG,
+                      "every buffer must be device memory of the current device (nothing is staged)");
+
+    // scratch layout: result keys, counters, totals, removal bits, visited
+    // sets (these only when they do not fit in shared memory)
+    const size_t words = (size_t)((n + 31) / 32);
+    const bool vis_off_chip = !search_visited_on_chip((uint32_t)n);
+    const size_t off_keys = 0;
+    const size_t off_ctr = off_keys + round_up((size_t)m * k_out * sizeof(uint64_t));
+    const size_t off_tot = off_ctr + round_up((size_t)m * NCTR * sizeof(long long));
+    const size_t off_rem = off_tot + round_up(NTOT * sizeof(unsigned long long));
+    const size_t off_vis = off_rem + round_up(words * sizeof(uint32_t));
+    const size_t need = off_vis + (vis_off_chip ? round_up((size_t)m * words * sizeof(uint32_t)) : 0);
+    if (need > kScratchBytes)
+        return reject(KNN_ERR_CAPACITY,
+                      "m = %lld queries over n = %lld nodes need %zu bytes of scratch; the fixed "
+                      "array holds %zu (about m * n / 8 bytes are needed once n exceeds the "
+                      "on-chip visited sets): use fewer queries per call",
+                      (long long)m, (long long)n, need, kScratchBytes);
+
     unsigned char *scratch = nullptr;
     knn_status st = scratch_on(device, &scratch);
     if (st != KNN_OK) return st;
@@ -124,7 +142,7 @@ extern "C" KNN_API knn_status knn_search_noalloc(const float *rows, int64_t n, i
     long long *counters = reinterpret_cast<long long *>(scratch + off_ctr);
     unsigned long long *totals = reinterpret_cast<unsigned long long *>(scratch + off_tot);
     uint32_t *removed = reinterpret_cast<uint32_t *>(scratch + off_rem);
-    uint32_t *visited = reinterpret_cast<uint32_t *>(scratch + off_vis);
+    uint32_t *visited = vis_off_chip ? reinterpret_cast<uint32_t *>(scratch + off_vis) : nullptr;
     cudaError_t e = cudaMemsetAsync(scratch + off_tot, 0, need - off_tot, s);
     if (e != cudaSuccess) return reject(KNN_ERR_CUDA, "clearing the scratch failed: %s", cudaGetErrorString(e));
 

@@ -358,7 +358,9 @@ ignns_search_kernel(const SearchArgs a) {
                     // round trip as their rows (lane l: entry pf_p of neighbour
                     // pf_j), so a move to one of them needs no list load
                     const int32_t nbj = __shfl_sync(FULL, nb, pf_j);
-                    const int32_t pfl = (pf_j < npf && nbj >= 0) ? (int32_t)ld_nc_u32(a.nbr + (size_t)nbj * a.k + pf_p) : -1;
+                    // (an entry outside the node range is an empty slot: no list read)
+                    const int32_t pfl = (pf_j < npf && (uint32_t)nbj - lo < np)
+                                            ? (int32_t)ld_nc_u32(a.nbr + (size_t)nbj * a.k + pf_p) : -1;
                     // only the rows the step can evaluate load; as many passes
                     // as the k rows need (one pass holds 32 / G rows)
                     const uint32_t nrow = ((um >> lane) & 1u) ? (uint32_t)nb : GATHER_SKIP;

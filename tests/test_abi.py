@@ -133,3 +133,24 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     with pytest.raises(ImportError):
         k._load_library()
     importlib.reload(b)
+
+
+def test_noalloc_search_checks_alignment_before_any_device_work(knn):
+    """Rows and queries are read with 16-byte loads: a misaligned pointer is
+    refused by pointer arithmetic alone, before any CUDA call (here there is
+    no GPU, and the pointers are never dereferenced)."""
+    lib = knn.lib
+    base = 1 << 20
+    args = dict(rows=base, n=1000, dim=16, nbr=base, k=4, q=base, m=8, k_out=4, ids=base,
+                sims=base)
+
+    def call(**kw):
+        a = dict(args, **kw)
+        return lib.knn_search_noalloc(a["rows"], a["n"], a["dim"], a["nbr"], a["k"], a["q"], a["m"],
+                                      a["k_out"], 4.0, 5.0, 1, 0, a["ids"], a["sims"], None)
+
+    for bad in (dict(rows=base + 4), dict(q=base + 8), dict(nbr=base + 2), dict(ids=base + 4),
+                dict(sims=base + 1)):
+        assert call(**bad) == knn.KNN_ERR_INVALID_ARG, bad
+        msg = lib.knn_last_error().decode()
+        assert "boundary" in msg or "aligned" in msg, msg

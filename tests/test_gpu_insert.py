@@ -6,8 +6,7 @@
   decisions include a near tie within FP32 rounding.
 * Batches: the edge recall of the GPU graph against the exact graph must be
   within 0.01 of the sequential oracle's recall on the same stream.
-* Full size (100,000 + 1,024-point batches at d = 128): properties that hold
-  at any size, checked against the oracle one pair at a time.
+* The full-size launch shapes are in test_gpu_full_size.py.
 """
 import math
 
@@ -46,21 +45,29 @@ def edges(g, n, k):
     return ids.cpu().numpy(), sims.cpu().numpy()
 
 
-@pytest.mark.parametrize("speedup,depth", [(4.0, 2), (20.0, 2), (4.0, 1), (4.0, 3), (8.0, 5)])
-def test_single_point_inserts_match_sequential_oracle(knn, speedup, depth):
-    """Both sides start from the oracle's exact graph.  After every insert the
-    whole GPU graph must equal the oracle's, and the insert's counters and new
-    list must match; the comparison stops only where the graphs part at an
-    insert whose decisions the oracle flags as a near tie."""
+def oracle_graph(X0, ids, sims, capacity):
+    """An oracle graph (Algorithm 1's state) over X0 with the given lists."""
+    n, d = X0.shape
+    og = oracle.Graph(d, ids.shape[1], capacity)
+    og.X[:n] = X0
+    og.ids[:n] = ids
+    og.sims[:n] = sims
+    og.n = n
+    return og
+
+
+def single_point_inserts(knn, og, Xs, speedup, e, seed, depth, min_compared, label):
+    """Insert Xs one point at a time on both sides, starting from the oracle
+    graph og (restored on the GPU).  After every insert the whole GPU graph
+    must equal the oracle's, and the insert's counters and new list must
+    match; the comparison stops only where the graphs part at an insert whose
+    decisions the oracle flags as a near tie.  Returns the inserts compared."""
     import torch
-    W = SMALL_D16
-    X0, Xs = W.initial(), W.stream(250)
-    k, e, seed = W.k, W.expansion, W.seed_search
-    n0 = X0.shape[0]
-    tol = gather_tol(W.mixture.d)
-    og = oracle.Graph.exact(X0, k, capacity=n0 + len(Xs))
-    og.X[n0:] = Xs
-    g = make_graph(knn, X0, k, speedup, e, seed, n0 + len(Xs), 1, depth, nbr_ids=og.ids[:n0])
+    n0, k, d = og.n, og.k, og.d
+    og.X[n0:n0 + len(Xs)] = Xs
+    tol = gather_tol(d)
+    g = make_graph(knn, og.X[:n0], k, speedup, e, seed, n0 + len(Xs), 1, depth,
+                   nbr_ids=og.ids[:n0])
     compared = 0
     try:
         ctr = np.empty((1, 8), np.int64)
@@ -85,7 +92,30 @@ def test_single_point_inserts_match_sequential_oracle(knn, speedup, depth):
             compared += 1
     finally:
         g.close()
-    assert compared >= 50, f"only {compared} inserts compared"
+        og.n = n0 + compared
+    print(f"{label}: {compared} of {len(Xs)} single-point inserts equal the oracle, whole graph")
+    assert compared >= min_compared, f"only {compared} inserts compared"
+    return compared
+
+
+@pytest.mark.parametrize("speedup,depth", [(4.0, 2), (20.0, 2), (4.0, 1), (4.0, 3), (8.0, 5)])
+def test_single_point_inserts_match_sequential_oracle(knn, speedup, depth):
+    """Both sides start from the oracle's exact graph (d = 16)."""
+    W = SMALL_D16
+    X0, Xs = W.initial(), W.stream(250)
+    og = oracle.Graph.exact(X0, W.k, capacity=X0.shape[0] + len(Xs))
+    single_point_inserts(knn, og, Xs, speedup, W.expansion, W.seed_search, depth, 50,
+                         f"d16 speedup {speedup:g} DEPTH {depth}")
+
+
+def test_single_point_inserts_d128(knn):
+    """d = 128 (the benchmark's dimension): 3,000 initial points of the
+    benchmark's mixture, 100 points inserted one at a time."""
+    W = PLAIN_D128
+    X0 = W.mixture.sample(3000, 71)
+    Xs = W.mixture.sample(100, 72)
+    og = oracle.Graph.exact(X0, W.k, capacity=3100)
+    single_point_inserts(knn, og, Xs, 4.0, W.expansion, W.seed_search, 2, 50, "d128")
 
 
 def _recall(ids, exact):
@@ -125,6 +155,41 @@ def test_batched_inserts_recall_matches_sequential(knn, batch, depth):
     assert st["inserts"] == na and st["update_evals"] <= na * sum(k ** t for t in range(2, depth + 1))
 
 
+def test_batched_inserts_recall_d128(knn):
+    """The benchmark's form at a size the oracle finishes in seconds: 20,000
+    initial points of the d = 128 mixture, then 8 batches of 1,024.  Batches
+    (C14) search the graph as it stood before the batch, so their lists
+    differ from the sequential build's; the edge recall against the exact
+    graph, over all lists and over the inserted points' lists alone, must be
+    within 0.01 of the sequential oracle's (Algorithm 1, one point at a time)
+    on the same stream."""
+    W = PLAIN_D128
+    n0, na, B = 20_000, 8 * 1024, 1024
+    X0, Xs = W.mixture.sample(n0, 81), W.mixture.sample(na, 82)
+    k, speedup, e, seed = W.k, 4.0, W.expansion, W.seed_search
+    X = np.vstack([X0, Xs])
+    og = oracle.Graph.exact(X0, k, capacity=n0 + na)
+    o_start = og.ids[:n0].copy()
+    og.insert_stream(Xs, speedup, e, 2, seed)
+    exact, _, _ = oracle.exact_knn(X, k)
+    r_seq = _recall(og.ids, exact)
+    r_seq_new = _recall(og.ids[n0:], exact[n0:])
+
+    g = make_graph(knn, X0, k, speedup, e, seed, n0 + na, B, 2, nbr_ids=o_start)
+    try:
+        for b0 in range(0, na, B):
+            g.insert(cuda_tensor(Xs[b0:b0 + B]))
+        got, _ = edges(g, n0 + na, k)
+    finally:
+        g.close()
+    r_gpu = _recall(got, exact)
+    r_gpu_new = _recall(got[n0:], exact[n0:])
+    print(f"d128 batches of {B}: edge recall {r_gpu:.4f} (sequential oracle {r_seq:.4f}); "
+          f"inserted lists {r_gpu_new:.4f} (oracle {r_seq_new:.4f})")
+    assert abs(r_gpu - r_seq) <= 0.01, (r_gpu, r_seq)
+    assert abs(r_gpu_new - r_seq_new) <= 0.01, (r_gpu_new, r_seq_new)
+
+
 def test_insert_edge_cases(knn):
     """The smallest graph (n = k+1), a ragged last batch, and a full graph."""
     import torch
@@ -146,42 +211,6 @@ def test_insert_edge_cases(knn):
     assert got.min() >= 0 and got.max() < 56
     exact, _, _ = oracle.exact_knn(X, 10)
     assert _recall(got, exact) > 0.8
-
-
-def test_full_size_batch_properties(knn):
-    """100,000 points at d = 128, two 1,024-point batches as the benchmark
-    times them: every search spends exactly B = floor(n/4); Update computes at
-    most k^2 new similarities per point; every list of a new point and of a
-    sample of old points holds k distinct ids with the oracle's similarities,
-    sorted; no old list's k-th similarity decreases."""
-    import torch
-    W = PLAIN_D128
-    X0 = W.initial()
-    Xs = W.stream(2048)
-    k = W.k
-    n0 = X0.shape[0]
-    g = make_graph(knn, X0, k, 4.0, W.expansion, W.seed_search, n0 + 2048, 1024)
-    try:
-        before_ids, before_sims = edges(g, n0, k)
-        ctr = np.empty((1024, 8), np.int64)
-        for b in range(2):
-            g.insert(cuda_tensor(Xs[b * 1024:(b + 1) * 1024]))
-            g.counters(ctr)
-            n = n0 + b * 1024
-            assert np.all(ctr[:, 0] == math.floor(n / 4.0))
-            assert np.all(ctr[:, 1] <= k * k)
-        ids, sims = edges(g, n0 + 2048, k)
-    finally:
-        g.close()
-    X = np.vstack([X0, Xs])
-    assert np.all(sims[:n0, -1] >= before_sims[:, -1])
-    rng = np.random.default_rng(2)
-    rows = np.concatenate([rng.choice(n0, 24, replace=False), n0 + rng.choice(2048, 24, replace=False)])
-    for u in rows:
-        assert len(set(ids[u])) == k and u not in ids[u]
-        want = [oracle.similarity(X[u], X[v]) for v in ids[u]]
-        assert rel_err(sims[u], want).max() <= 1e-5
-        assert np.all(np.diff(sims[u]) <= 0)
 
 
 @pytest.mark.parametrize("m", [64, 1000])

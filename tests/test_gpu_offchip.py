@@ -1,0 +1,70 @@
+"""Graphs above 225,280 nodes, where a query's visited set (Sec. 3: no
+similarity computed twice) and an Update walk's set of seen nodes
+(Algorithm 2) no longer fit in shared memory: the search keeps its bitsets in
+global memory (set with L2 atomics, read from L2) and Update its seen sets
+likewise.  Both paths are held to the same bar as the on-chip ones: bit-exact
+ids and counters against the oracle for every query or insert whose
+decisions the oracle does not flag as a near tie, and after each single-point
+insert the whole graph equal to the oracle's.
+
+Graph: 240,000 points of d = 16 from a 60-component Gaussian mixture (means
+in [-10, 10]^16, sigma 1); its lists are the oracle's exact 10-nn lists
+within each component (cheap to build, and a valid k-nn graph for the search
+whatever the components' overlap).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1602_06819_gb300.inputs import Mixture
+from test_gpu_insert import oracle_graph, single_point_inserts
+from test_gpu_search import compare
+
+pytestmark = pytest.mark.gpu
+
+N, K = 240_000, 10
+
+
+@pytest.fixture(scope="module")
+def knn():
+    from paper_1602_06819_gb300 import build
+    build.build()
+    from paper_1602_06819_gb300 import knn as module
+    return module
+
+
+@pytest.fixture(scope="module")
+def clustered():
+    mix = Mixture(d=16, components=60, half_width=10.0, sigma=1.0, seed=61)
+    X, labels = mix.sample(N, 1, with_labels=True)
+    ids = np.full((N, K), -1, np.int64)
+    sims = np.full((N, K), -np.inf)
+    for c in range(mix.components):
+        idx = np.flatnonzero(labels == c)
+        ci, cs, _ = oracle.exact_knn(X[idx], K)
+        ids[idx] = idx[ci]
+        sims[idx] = cs
+    return mix, X, ids, sims
+
+
+def test_graph_is_above_the_shared_memory_limit():
+    """The kernels keep 4 queries' (or Update walks') bitsets per block within
+    110 KiB of shared memory; at 240,000 nodes they need more."""
+    assert 4 * ((N + 31) // 32) * 4 > 110 * 1024 >= 4 * ((225_280 + 31) // 32) * 4
+
+
+@pytest.mark.parametrize("storage,m,amb", [(0, 64, 5), (1, 32, 3)])
+def test_offchip_queries(knn, clustered, storage, m, amb):
+    mix, X, ids, _ = clustered
+    Q = mix.sample(m, 3)
+    compare(knn, X, Q, K, K, 16.0, 5.0, seed=4, storage=storage, o_ids=ids, max_ambiguous=amb,
+            label=f"off-chip visited sets, storage {storage}")
+
+
+def test_offchip_single_point_inserts(knn, clustered):
+    """Each insert's Update walk (DEPTH 2) marks its seen nodes in global
+    memory; 16 inserts, the whole 240,000-node graph compared after each (the
+    oracle flags none of them as a near tie)."""
+    mix, X, ids, sims = clustered
+    og = oracle_graph(X, ids, sims, N + 16)
+    single_point_inserts(knn, og, mix.sample(16, 5), 16.0, 5.0, 4, 2, 16, "off-chip seen sets")
