@@ -22,7 +22,7 @@
  *                         current node is evaluated and the search moves to
  *                         the most similar one).
  *   orc_update         -- Update (Algorithm 2): walk from the found neighbours
- *                         to a fixed DEPTH and add `new` to lists "if needed".
+ *                         to a fixed DEPTH and offer `new` to the lists met.
  *   orc_insert_stream  -- the sequential online build (Algorithm 1), one new
  *                         point at a time: iGNNS, then Update.
  *   orc_rescore        -- exact re-scoring of screening candidates (the
@@ -75,9 +75,10 @@
  *                again); lists are read before `new` is offered to them;
  *                the next level is the distinct ids gathered, minus nodes
  *                already seen, minus `new`, minus removed nodes.
- *   offer        "if needed, add new": if the id is absent and the list has
- *                a free slot or the candidate is better than its last entry,
- *                insert it in sorted position and drop the entry past k.
+ *   offer        the new node enters a list when its id is absent and the
+ *                list has a free slot or the candidate is better than its
+ *                last entry: it is placed in sorted position and the entry
+ *                pushed past k drops out.
  *
  * Decision margins: every floating-point decision records its relative
  * margin, so that a test can tell a genuine mismatch from a near tie that
@@ -468,9 +469,11 @@ typedef struct {
     double min_margin;      /* smallest relative gap between `new` and an entry  */
 } orc_update_stats;
 
-/* "If needed, add new to the neighborlist of node" (Algorithm 2).  Returns 1
- * if the list changed.  The margin is the smallest relative gap between s
- * and any entry of the list (a near tie there may place `new` differently). */
+/* The offer rule of Update (Algorithm 2): `id` joins the list when it is not
+ * in it yet and the list has a free slot or `id` ranks above the last entry;
+ * the entry pushed past k drops out.  Returns 1 if the list changed.  The
+ * margin is the smallest relative gap between s and any entry of the list
+ * (a near tie there may place `id` differently). */
 static int offer_to_list(int64_t *ids, double *sims, int32_t k, double s, int64_t id,
                          double *margin)
 {
@@ -502,12 +505,14 @@ static int cmp_i64(const void *a, const void *b)
 }
 
 /*
- * Update(graph, new, neighborlist) for a new node already stored at row
- * new_id of X, whose own list the caller has set.  L_ids/L_sims: the
- * neighbour list found by the search, best first (L_len entries).
+ * Update (Algorithm 2) for a new node already stored at row new_id of X,
+ * whose own list the caller has set: a breadth-first walk of at most `depth`
+ * levels that starts at the neighbours the search found and offers the new
+ * node to the list of every node it reaches.  L_ids/L_sims: the search's
+ * result, best first (L_len entries).
  *
- * depth: DEPTH of Algorithm 2.  full != 0 replaces the walk by an offer to
- * every live node (used only to check the offer rule against brute force).
+ * full != 0 replaces the walk by an offer to every live node (used only to
+ * check the offer rule against brute force).
  */
 void orc_update(const float *X, int64_t n_total, int32_t d,
                 int64_t *nbr_ids, double *nbr_sims, int32_t k,
@@ -534,62 +539,63 @@ void orc_update(const float *X, int64_t n_total, int32_t d,
     uint8_t *seen = (uint8_t *)calloc((size_t)n_total, 1);
     seen[new_id] = 1;
 
-    /* Q.addAll(neighborlist) */
-    int64_t q_len = 0, q_cap = L_len > 0 ? L_len : 1;
-    int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * (size_t)q_cap);
-    double *Q_sims = (double *)malloc(sizeof(double) * (size_t)q_cap);
+    /* level 1: the nodes of the search result, with the search's similarities */
+    int64_t lv_len = 0, lv_cap = L_len > 0 ? L_len : 1;
+    int64_t *lv_ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)lv_cap);
+    double *lv_sims = (double *)malloc(sizeof(double) * (size_t)lv_cap);
     for (int32_t i = 0; i < L_len; ++i) {
         if (L_ids[i] < 0 || seen[L_ids[i]]) continue;
         seen[L_ids[i]] = 1;
-        Q[q_len] = L_ids[i];
-        Q_sims[q_len] = L_sims[i];
-        ++q_len;
+        lv_ids[lv_len] = L_ids[i];
+        lv_sims[lv_len] = L_sims[i];
+        ++lv_len;
     }
 
-    for (int32_t level = 1; level <= depth && q_len > 0; ++level) {
-        int64_t next_len = 0, next_cap = q_len * k;
-        int64_t *Q_next = (int64_t *)malloc(sizeof(int64_t) * (size_t)(next_cap > 0 ? next_cap : 1));
-        for (int64_t qi = 0; qi < q_len; ++qi) {
-            int64_t node = Q[qi];
+    for (int32_t level = 1; level <= depth && lv_len > 0; ++level) {
+        int64_t got = 0, got_cap = lv_len * k;
+        int64_t *gathered = (int64_t *)malloc(sizeof(int64_t) * (size_t)(got_cap > 0 ? got_cap : 1));
+        for (int64_t li = 0; li < lv_len; ++li) {
+            int64_t node = lv_ids[li];
             int64_t *list_ids = nbr_ids + node * k;
             double *list_sims = nbr_sims + node * k;
-            /* Q_next.addAll(neighbors of node) -- read before offering */
+            /* the node's list feeds the next level; it is read before the
+             * new node is offered to it */
             if (level < depth)
                 for (int32_t i = 0; i < k; ++i)
-                    if (list_ids[i] >= 0) Q_next[next_len++] = list_ids[i];
-            /* compute similarity(new, node) -- level 1 reuses the search's */
+                    if (list_ids[i] >= 0) gathered[got++] = list_ids[i];
+            /* level 1 takes the search's similarity, deeper levels compute it */
             double s;
             if (level == 1) {
-                s = Q_sims[qi];
+                s = lv_sims[li];
             } else {
                 s = similarity(x_new, X + node * d, d);
                 st->evals++;
             }
             st->literal_evals++;
-            /* if needed, add new to the neighborlist of node */
             st->offers_taken += offer_to_list(list_ids, list_sims, k, s, new_id,
                                               &st->min_margin);
         }
-        /* Q <- distinct(Q_next) minus seen, new and removed nodes */
-        qsort(Q_next, (size_t)next_len, sizeof(int64_t), cmp_i64);
-        free(Q);
-        free(Q_sims);
-        q_cap = next_len > 0 ? next_len : 1;
-        Q = (int64_t *)malloc(sizeof(int64_t) * (size_t)q_cap);
-        Q_sims = (double *)malloc(sizeof(double) * (size_t)q_cap);
-        q_len = 0;
-        for (int64_t i = 0; i < next_len; ++i) {
-            int64_t w = Q_next[i];
+        /* the next level: each gathered id once, in ascending order, leaving
+         * out nodes already seen (the new node among them) and removed ones */
+        qsort(gathered, (size_t)got, sizeof(int64_t), cmp_i64);
+        free(lv_ids);
+        free(lv_sims);
+        lv_cap = got > 0 ? got : 1;
+        lv_ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)lv_cap);
+        lv_sims = (double *)malloc(sizeof(double) * (size_t)lv_cap);
+        lv_len = 0;
+        for (int64_t i = 0; i < got; ++i) {
+            int64_t w = gathered[i];
             if (seen[w] || (removed && removed[w])) continue;
             seen[w] = 1;
-            Q[q_len] = w;
-            Q_sims[q_len] = NAN;
-            ++q_len;
+            lv_ids[lv_len] = w;
+            lv_sims[lv_len] = NAN;
+            ++lv_len;
         }
-        free(Q_next);
+        free(gathered);
     }
-    free(Q);
-    free(Q_sims);
+    free(lv_ids);
+    free(lv_sims);
     free(seen);
 }
 
@@ -607,9 +613,10 @@ typedef struct {
 
 /*
  * Add the m points stored at rows n0 .. n0+m-1 of X to the graph whose first
- * n0 rows are built, one at a time: neighborlist = iGNNS(graph, new, k);
- * Update(graph, new, neighborlist).  The search of point i sees n0+i nodes
- * and uses stream = its id.  nbr_ids/nbr_sims have room for n0+m rows.
+ * n0 rows are built, one at a time: each point is searched with iGNNS, its
+ * list is the result, and Update then walks from that result.  The search
+ * of point i sees n0+i nodes and uses stream = its id.  nbr_ids/nbr_sims
+ * have room for n0+m rows.
  */
 void orc_insert_stream(const float *X, int64_t n0, int64_t m, int32_t d,
                        int64_t *nbr_ids, double *nbr_sims, int32_t k,

@@ -3,8 +3,8 @@
 //
 // Algorithm 2 walks from the neighbours found by the search: each node popped
 // at depth d has its list read (for depth d+1), gets sim(new, node) computed
-// and receives `new` "if needed".  For a batch of m new points this runs in
-// three kernels and never waits on a lock:
+// and is offered `new` (it enters when it ranks in the list's best k).  For a
+// batch of m new points this runs in three kernels and never waits on a lock:
 //
 //   cross   one warp per new point: its list = the best k of its search
 //           result and the exact similarities to the other m-1 points of the
@@ -21,7 +21,7 @@
 //           list and its chain, written back sorted.  The best k of a set
 //           under a strict total order does not depend on the order the
 //           candidates arrived in, so the result is the same as any sequence
-//           of "if needed, add new" steps.
+//           of single offers.
 //
 // Points of the batch appear in each other's lists through the cross-merge
 // only: the offers kernel offers `new` to nodes that existed before the batch.
@@ -265,7 +265,7 @@ __device__ __forceinline__ void offers_item(const UpdateArgs &a, int i, int lane
             }
             if (nhi > a.frontier_cap) nhi = (int)a.frontier_cap;
             __syncwarp();
-            // compute sim(new, node) for the level and offer `new` if needed
+            // compute sim(new, node) for the level and offer `new` to the node
             for (int f0 = hi; f0 < nhi; f0 += 32) {
                 const int nr = nhi - f0 < 32 ? nhi - f0 : 32;
                 const uint32_t w = lane < nr ? (uint32_t)level[f0 + lane] : 0u;

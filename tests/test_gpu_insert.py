@@ -219,7 +219,7 @@ def test_hub_node_under_contention(knn, m):
     right next to node w (exhaustive search, so w is in every point's level
     1) all offer themselves to w at once through its atomicExch chain; the
     merged list of w must be the best k of its old list and the m points
-    (Algorithm 2's "if needed, add new" applied in any order)."""
+    (Algorithm 2's offer rule applied in any order)."""
     import torch
     mix = Mixture(d=32, components=5, half_width=10.0, sigma=1.0, seed=19)
     n0, k = 1500, 10

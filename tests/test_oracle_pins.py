@@ -286,8 +286,8 @@ def test_update_hand_traces(orc):
 def test_full_update_gives_exact_graph(orc, n, d, k, seed):
     """Adding one point can only displace entries: an exact graph on n points,
     the exact list of the new point, and an offer to every node give the exact
-    graph on n+1 points.  This checks the offer rule ("if needed, add new",
-    Algorithm 2) against brute force."""
+    graph on n+1 points.  This checks Algorithm 2's offer rule against brute
+    force."""
     mix = Mixture(d=d, components=4, half_width=6.0, sigma=1.0, seed=seed)
     X = mix.sample(n + 1, seed + 10)
     ids, sims, _ = orc.exact_knn(X[:n], k)
