@@ -319,6 +319,22 @@ KNN_API knn_status knn_exact_last_info(knn_exact_info *out);
 KNN_API knn_status knn_exact_set_wait_limit(int64_t ns);
 
 /*
+ * Grow a graph to hold `capacity` nodes (nothing happens if it already
+ * does), keeping its nodes, lists, removals and counters.  The paper has no
+ * counterpart: its graph takes a flow of points without a stated bound
+ * (Sec. 1), and this lets the device graph follow that flow as far as
+ * device memory allows instead of stopping at the capacity fixed at
+ * creation.  The per-node arrays (rows, screening copy, lists, removal bits,
+ * Update chain heads, the visited sets of one batch) are allocated anew for
+ * `capacity` and the nodes copied over, so the new arrays' bytes must be free
+ * on top of the old ones, plus `headroom_bytes` (>= 0) that must stay free
+ * afterwards; otherwise KNN_ERR_OOM and the graph is unchanged.  capacity
+ * must be below 2^31 (KNN_ERR_CAPACITY).  Waits for every stream the graph
+ * used and for `stream`, and returns when the graph is ready.
+ */
+KNN_API knn_status knn_graph_reserve(knn_graph *g, int64_t capacity, int64_t headroom_bytes, void *stream);
+
+/*
  * The query search of knn_graph_query_batch (FP32 rows, no removed nodes)
  * over a graph held in the caller's own device buffers, without any device
  * allocation.  The paper has no counterpart: this exists for callers that
@@ -410,6 +426,14 @@ typedef struct knn_server knn_server;
 typedef struct knn_server_params {
     int32_t k_out;           /* neighbours returned per query point, 1..k           */
     int32_t max_step_points; /* points per step, 1..max_batch (0: max_batch)        */
+    int64_t grow_headroom_bytes; /* admission by free device memory: when an insert
+                                    does not fit the graph's capacity, the worker
+                                    grows the graph (knn_graph_reserve, by half its
+                                    capacity or to what the insert needs) as long
+                                    as this many bytes stay free afterwards; an
+                                    insert that cannot be admitted so fails with
+                                    KNN_ERR_OOM.  0: the capacity is fixed and
+                                    such an insert fails with KNN_ERR_CAPACITY    */
 } knn_server_params;
 
 typedef enum knn_request_kind { KNN_REQ_INSERT = 0, KNN_REQ_QUERY = 1 } knn_request_kind;
@@ -429,6 +453,8 @@ typedef struct knn_server_stats {
     int64_t epoch;              /* insert steps committed                             */
     int64_t max_queue;          /* most requests waiting at once                      */
     double busy_ms;             /* device time of all steps (CUDA events)            */
+    int64_t grows;              /* times the graph was grown for admission            */
+    int64_t capacity;           /* the graph's capacity now                          */
 } knn_server_stats;
 
 /* Start a server on g (which it then owns until knn_server_destroy: make no

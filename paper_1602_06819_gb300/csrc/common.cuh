@@ -348,6 +348,10 @@ struct RowGatherHead {
     }
 };
 
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // The row layout with passes for MAX_ROWS rows (rounded up to whole passes)
 // in flight.
 template <int STORAGE, int DP, int MAX_ROWS>

@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -696,6 +697,154 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
             CU(cudaStreamSynchronize(s));
         }
     }
+    return KNN_OK;
+}
+
+// Replace the allocation `old` of g by `fresh` (already counted in g->bytes).
+static void swap_allocation(knn_graph *g, void *old, void *fresh, size_t old_bytes) {
+    for (void *&p : g->allocations)
+        if (p == old) {
+            p = fresh;
+            cudaFree(old);
+            g->bytes -= old_bytes;
+            return;
+        }
+}
+
+// Bytes of the per-node arrays of a graph with `capacity` nodes (the rows,
+// the screening copy, the lists, the removal bits, the Update chain heads and
+// the batch's visited sets).
+static size_t node_bytes(const knn_graph *g, int64_t capacity) {
+    const size_t C = (size_t)capacity, DP = (size_t)g->dp, K = (size_t)g->p.k;
+    const size_t words = (C + 31) / 32;
+    size_t b = C * DP * 4 + C * K * 8 + words * 4 + C * 4 + (size_t)g->p.max_batch * words * 4;
+    if (g->p.storage == KNN_STORAGE_BF16) b += C * DP * 2;
+    if (g->p.storage == KNN_STORAGE_FP8_E4M3) b += C * DP + C * 4;
+    return b;
+}
+
+KNN_API knn_status knn_graph_reserve(knn_graph *g, int64_t capacity, int64_t headroom_bytes, void *stream) {
+    NvtxRange nvtx_range("knn_graph_reserve");
+    if (!g) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (capacity <= g->p.capacity) return KNN_OK;
+    if (capacity >= (int64_t)INT32_MAX) return fail(KNN_ERR_CAPACITY, "capacity must stay below 2^31");
+    if (headroom_bytes < 0) return fail(KNN_ERR_INVALID_ARG, "headroom_bytes must be >= 0");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // nothing of the graph may be in flight while its arrays move
+    CU(cudaStreamSynchronize(g->last_stream));
+    CU(cudaStreamSynchronize(g->side));
+    CU(cudaStreamSynchronize(s));
+    const size_t need = node_bytes(g, capacity);
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    if (need + (size_t)headroom_bytes > free_b)
+        return fail(KNN_ERR_OOM, "growing to %lld nodes needs %zu bytes with %lld of headroom; %zu free",
+                    (long long)capacity, need, (long long)headroom_bytes, free_b);
+    const int64_t C0 = g->p.capacity, C = capacity, n = g->n, K = g->p.k, DP = g->dp, M = g->p.max_batch;
+    const int64_t w0 = g->vwords, w = (C + 31) / 32;
+    // new arrays first, so that a failure leaves the graph as it was
+    float *X = nullptr, *nbr_d2 = nullptr, *scale = nullptr;
+    uint16_t *Xb = nullptr;
+    uint8_t *X8 = nullptr;
+    int32_t *nbr_ids = nullptr, *head = nullptr;
+    uint32_t *removed = nullptr, *visited = nullptr;
+    std::vector<void *> fresh;
+    auto get = [&](auto **ptr, size_t count) -> bool {
+        void *q = nullptr;
+        const size_t bytes = std::max<size_t>(count * sizeof(**ptr), 16);
+        if (cudaMalloc(&q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        fresh.push_back(q);
+        *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q);
+        return true;
+    };
+    bool ok = get(&X, C * DP) && get(&nbr_ids, C * K) && get(&nbr_d2, C * K) && get(&removed, w) &&
+              get(&head, C) && get(&visited, M * w);
+    if (ok && g->Xb) ok = get(&Xb, C * DP);
+    if (ok && g->X8) ok = get(&X8, C * DP) && get(&scale, C);
+    // Update's level bound (k + k^2 + ... + k^DEPTH, at most the nodes plus
+    // k) grows with the graph while the graph is smaller than it
+    int64_t levels = 0, pw = 1;
+    for (int t = 1; t <= g->p.depth; ++t) {
+        pw = std::min<int64_t>(pw * K, C + K);
+        levels = std::min<int64_t>(levels + pw, C + K);
+    }
+    const bool regrow = levels > g->frontier_cap;
+    const unsigned ocap = (unsigned)(M * (K + levels));
+    uint64_t *okey = nullptr;
+    int32_t *onext = nullptr, *touched = nullptr, *frontier = nullptr;
+    if (ok && regrow)
+        ok = (double)M * (double)(K + levels) < 4.0e9 && get(&okey, ocap) && get(&onext, ocap) &&
+             get(&touched, ocap) && get(&frontier, M * levels);
+    if (!ok) {
+        for (void *q : fresh) cudaFree(q);
+        return fail(KNN_ERR_OOM, "growing to %lld nodes: cudaMalloc failed", (long long)capacity);
+    }
+    auto moves = [&]() -> knn_status {
+        CU(cudaMemcpyAsync(X, g->X, (size_t)n * DP * 4, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemsetAsync(X + n * DP, 0, (size_t)(C - n) * DP * 4, s));
+        if (g->Xb) CU(cudaMemcpyAsync(Xb, g->Xb, (size_t)n * DP * 2, cudaMemcpyDeviceToDevice, s));
+        if (g->X8) {
+            CU(cudaMemcpyAsync(X8, g->X8, (size_t)n * DP, cudaMemcpyDeviceToDevice, s));
+            CU(cudaMemcpyAsync(scale, g->scale, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+        }
+        CU(cudaMemcpyAsync(nbr_ids, g->nbr_ids, (size_t)n * K * 4, cudaMemcpyDeviceToDevice, s));
+        CU(launch_fill_i32(nbr_ids + n * K, -1, (C - n) * K, s));
+        CU(cudaMemcpyAsync(nbr_d2, g->nbr_d2, (size_t)n * K * 4, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemsetAsync(removed, 0, (size_t)w * 4, s));
+        CU(cudaMemcpyAsync(removed, g->removed, (size_t)w0 * 4, cudaMemcpyDeviceToDevice, s));
+        CU(launch_fill_i32(head, -1, C, s));  // every chain is empty between calls
+        g->launches += 2;
+        CU(cudaStreamSynchronize(s));
+        return KNN_OK;
+    };
+    knn_status st = moves();
+    if (st != KNN_OK) {
+        for (void *q : fresh) cudaFree(q);
+        return st;
+    }
+    const size_t b_rows = (size_t)C0 * DP * 4, b_list = (size_t)C0 * K * 4, b_bits = (size_t)w0 * 4;
+    g->bytes += node_bytes(g, C);
+    swap_allocation(g, g->X, X, b_rows);
+    swap_allocation(g, g->nbr_ids, nbr_ids, b_list);
+    swap_allocation(g, g->nbr_d2, nbr_d2, b_list);
+    swap_allocation(g, g->removed, removed, b_bits);
+    swap_allocation(g, g->head, head, (size_t)C0 * 4);
+    swap_allocation(g, g->visited, visited, (size_t)M * b_bits);
+    if (g->Xb) swap_allocation(g, g->Xb, Xb, (size_t)C0 * DP * 2);
+    if (g->X8) {
+        swap_allocation(g, g->X8, X8, (size_t)C0 * DP);
+        swap_allocation(g, g->scale, scale, (size_t)C0 * 4);
+    }
+    g->X = X;
+    g->Xb = Xb ? Xb : g->Xb;
+    g->X8 = X8 ? X8 : g->X8;
+    g->scale = scale ? scale : g->scale;
+    g->nbr_ids = nbr_ids;
+    g->nbr_d2 = nbr_d2;
+    g->removed = removed;
+    g->head = head;
+    g->visited = visited;
+    if (regrow) {
+        g->bytes += (size_t)ocap * 16 + (size_t)M * levels * 4;
+        swap_allocation(g, g->offer_key, okey, (size_t)g->offer_cap * 8);
+        swap_allocation(g, g->offer_next, onext, (size_t)g->offer_cap * 4);
+        swap_allocation(g, g->touched, touched, (size_t)g->offer_cap * 4);
+        swap_allocation(g, g->frontier, frontier, (size_t)M * g->frontier_cap * 4);
+        g->offer_key = okey;
+        g->offer_next = onext;
+        g->touched = touched;
+        g->frontier = frontier;
+        g->offer_cap = ocap;
+        g->frontier_cap = levels;
+    }
+    g->vwords = w;
+    g->removed_host.resize((size_t)w, 0u);
+    g->p.capacity = C;
+    g->last_stream = s;
     return KNN_OK;
 }
 

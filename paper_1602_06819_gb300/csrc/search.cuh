@@ -34,7 +34,10 @@
 // Visited sets.  A query's bitset lives in shared memory when the bitsets of
 // a block's warps fit two blocks on an SM (about 220,000 nodes); marks are
 // then shared-memory atomics and tests cost a few cycles.  Larger graphs keep
-// the bitset in global memory (L2 atomics, L2 reads).
+// the bitset in global memory (L2 atomics, L2 reads); there a climb step
+// loads its neighbours' visited bits in the same round trip as their rows
+// (rows of visited neighbours are loaded too), so that a step waits for one
+// memory latency instead of two.
 //
 // Every similarity computation is thus one the sequential search performs:
 // rows gathered ahead but not reached are not counted, marked or offered, and
@@ -350,10 +353,24 @@ ignns_search_kernel(const SearchArgs a) {
                     const bool valid = nb >= 0 && (uint32_t)nb - lo < np &&
                                        !(any_removed && test_bit_ro(a.removed, (uint32_t)nb));
                     __syncwarp();
-                    const bool seen = valid && vis.test((uint32_t)nb);
-                    unsigned um = __ballot_sync(FULL, valid && !seen);
-                    if (um == 0u) break;  // every neighbour visited: local maximum
-                    um = lowest_bits(um, limit - evals);
+                    unsigned um = 0u;
+                    uint32_t bw = 0u;
+                    if constexpr (!SMEM_VIS) {
+                        // global bits: they load in the round trip of the rows
+                        // (the rows of visited neighbours load too)
+                        if (valid) {
+                            bw = ld_cg_u32(vis.bits + (((uint32_t)nb - lo) >> 5));
+                            // and the neighbours' lists start towards L1 for a move
+                            const int32_t *l = a.nbr + (size_t)nb * a.k;
+                            prefetch_l1(l);
+                            prefetch_l1(l + a.k - 1);
+                        }
+                    } else {
+                        const bool seen = valid && vis.test((uint32_t)nb);
+                        um = __ballot_sync(FULL, valid && !seen);
+                        if (um == 0u) break;  // every neighbour visited: local maximum
+                        um = lowest_bits(um, limit - evals);
+                    }
                     // the lists of the first 32 / k neighbours load in the same
                     // round trip as their rows (lane l: entry pf_p of neighbour
                     // pf_j), so a move to one of them needs no list load
@@ -363,10 +380,17 @@ ignns_search_kernel(const SearchArgs a) {
                                             ? (int32_t)ld_nc_u32(a.nbr + (size_t)nbj * a.k + pf_p) : -1;
                     // only the rows the step can evaluate load; as many passes
                     // as the k rows need (one pass holds 32 / G rows)
-                    const uint32_t nrow = ((um >> lane) & 1u) ? (uint32_t)nb : GATHER_SKIP;
+                    const bool load = !SMEM_VIS ? valid : ((um >> lane) & 1u) != 0u;
+                    const uint32_t nrow = load ? (uint32_t)nb : GATHER_SKIP;
                     const float nd2 = a.k <= 12   ? gather_d2<STORAGE, DP, 12>(src, nrow, a.k, qv)
                                       : a.k <= 24 ? gather_d2<STORAGE, DP, 24>(src, nrow, a.k, qv)
                                                   : gather_d2<STORAGE, DP>(src, nrow, a.k, qv);
+                    if constexpr (!SMEM_VIS) {
+                        const bool seen = valid && ((bw >> (((uint32_t)nb - lo) & 31u)) & 1u);
+                        um = __ballot_sync(FULL, valid && !seen);
+                        if (um == 0u) break;  // every neighbour visited: local maximum
+                        um = lowest_bits(um, limit - evals);
+                    }
                     int mi;
                     unsigned evc;
                     if (a.climb == KNN_CLIMB_BEST) {

@@ -91,6 +91,8 @@ struct knn_server {
     uint64_t next_id = 0;
     bool stopping = false;
     int64_t pending_inserts = 0;  // insert points admitted into the step being formed
+    int64_t headroom = 0;         // bytes that must stay free when the graph grows (0: no growth)
+    bool grow_failed = false;     // the last growth for the insert at the queue head failed
     knn_server_stats stats{};
     std::thread worker;
 
@@ -137,6 +139,7 @@ void knn_server::run() {
     for (;;) {
         Slot &sl = slots[step & 1];
         finish(sl);  // the slot's previous step (t - 2) is done before it is reused
+        int64_t grow_to = 0;  // capacity an insert at the queue head needs
         {
             std::unique_lock<std::mutex> lk(mu);
             Slot &other = slots[(step + 1) & 1];
@@ -154,7 +157,8 @@ void knn_server::run() {
                 continue;
             }
             // admission: submission order, while the points fit the slot and
-            // the inserts fit the graph
+            // the inserts fit the graph (or, with a headroom set, the graph
+            // can be grown within free device memory)
             int64_t pts = 0;
             const auto now = Clock::now();
             while (!queue.empty()) {
@@ -162,12 +166,17 @@ void knn_server::run() {
                 if (pts + r->m > P) break;
                 if (r->kind == KNN_REQ_INSERT && shape.n + pending_inserts + r->m > shape.capacity) {
                     if (!sl.reqs.empty()) break;  // try again once this step has committed
+                    if (headroom > 0 && !grow_failed) {
+                        grow_to = shape.n + r->m;
+                        break;  // grow outside the lock, then admit again
+                    }
                     // can never fit: fail it
                     queue.pop_front();
-                    r->info.status = KNN_ERR_CAPACITY;
+                    r->info.status = headroom > 0 ? KNN_ERR_OOM : KNN_ERR_CAPACITY;
                     r->t_admit = now;
                     r->info.latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
                     r->done = true;
+                    grow_failed = false;
                     cv_done.notify_all();
                     continue;
                 }
@@ -177,7 +186,26 @@ void knn_server::run() {
                 pts += r->m;
                 if (r->kind == KNN_REQ_INSERT) pending_inserts += r->m;
             }
-            if (sl.reqs.empty()) continue;
+            if (sl.reqs.empty() && grow_to == 0) continue;
+        }
+        if (grow_to > 0) {
+            // nothing may be in flight while the graph's arrays move; grow by
+            // half the capacity, else just to what the insert needs
+            finish(slots[0]);
+            finish(slots[1]);
+            const int64_t big = std::min<int64_t>(std::max<int64_t>(grow_to, shape.capacity + shape.capacity / 2),
+                                                  (int64_t)INT32_MAX - 1);
+            knn_status st = knn_graph_reserve(g, big, headroom, comp);
+            if (st != KNN_OK && big > grow_to) st = knn_graph_reserve(g, grow_to, headroom, comp);
+            std::lock_guard<std::mutex> lk(mu);
+            if (st == KNN_OK) {
+                shape = graph_shape(g);
+                stats.grows += 1;
+                stats.capacity = shape.capacity;
+            } else {
+                grow_failed = true;  // the insert at the head fails at the next admission
+            }
+            continue;
         }
         // pack: queries first, then inserts
         const int d = shape.dim;
@@ -260,6 +288,9 @@ KNN_API knn_status knn_server_create(knn_graph *g, const knn_server_params *p, k
     s->shape = sh;
     s->k_out = p->k_out;
     s->P = P;
+    if (p->grow_headroom_bytes < 0) return server_fail(KNN_ERR_INVALID_ARG, "grow_headroom_bytes must be >= 0");
+    s->headroom = p->grow_headroom_bytes;
+    s->stats.capacity = sh.capacity;
     if (cudaGetDevice(&s->device) != cudaSuccess) return server_fail(KNN_ERR_CUDA, "no CUDA device");
     bool ok = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&s->comp, cudaStreamNonBlocking) == cudaSuccess &&

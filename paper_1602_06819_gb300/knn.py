@@ -46,6 +46,7 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
 # Every symbol include/knn_graph.h declares.
 EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
             "knn_graph_query_ids", "knn_graph_query_partitioned", "knn_graph_remove", "knn_graph_get_edges",
+            "knn_graph_reserve",
             "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
             "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
@@ -88,7 +89,8 @@ class KnnExactInfo(ctypes.Structure):
 
 
 class KnnServerParams(ctypes.Structure):
-    _fields_ = [("k_out", ctypes.c_int32), ("max_step_points", ctypes.c_int32)]
+    _fields_ = [("k_out", ctypes.c_int32), ("max_step_points", ctypes.c_int32),
+                ("grow_headroom_bytes", ctypes.c_int64)]
 
 
 class KnnRequestInfo(ctypes.Structure):
@@ -103,7 +105,8 @@ class KnnRequestInfo(ctypes.Structure):
 class KnnServerStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("requests", ctypes.c_int64), ("points", ctypes.c_int64),
                 ("inserts", ctypes.c_int64), ("queries", ctypes.c_int64), ("epoch", ctypes.c_int64),
-                ("max_queue", ctypes.c_int64), ("busy_ms", ctypes.c_double)]
+                ("max_queue", ctypes.c_int64), ("busy_ms", ctypes.c_double), ("grows", ctypes.c_int64),
+                ("capacity", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -129,6 +132,7 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_query_partitioned": (I32, [P, P, I64, I32, U64, P, I32, P, P, P]),
         "knn_graph_query_ids": (I32, [P, P, I64, I32, P, P, P, P]),
         "knn_graph_remove": (I32, [P, P, I64, P]),
+        "knn_graph_reserve": (I32, [P, I64, I64, P]),
         "knn_graph_get_edges": (I32, [P, P, P, I64, ctypes.POINTER(I64), P]),
         "knn_graph_last_counters": (I32, [P, P, I64, P]),
         "knn_graph_set_timing": (I32, [P, I32]),
@@ -266,6 +270,10 @@ def knn_graph_query_partitioned(g, vecs, k_out: int, query_id0: int, part_offset
 def knn_graph_remove(g, ids, stream=None) -> None:
     _check_dtype(ids, "int64", "ids")
     _check(lib.knn_graph_remove(g, _ptr(ids), ids.shape[0], _stream(stream)), "knn_graph_remove")
+
+
+def knn_graph_reserve(g, capacity: int, headroom_bytes: int = 0, stream=None) -> None:
+    _check(lib.knn_graph_reserve(g, capacity, headroom_bytes, _stream(stream)), "knn_graph_reserve")
 
 
 def knn_graph_get_edges(g, out_ids, out_sims=None, stream=None) -> int:
@@ -420,6 +428,10 @@ class Graph:
     def remove(self, ids, stream=None):
         knn_graph_remove(self.handle, ids, stream)
 
+    def reserve(self, capacity: int, headroom_bytes: int = 0, stream=None):
+        knn_graph_reserve(self.handle, capacity, headroom_bytes, stream)
+        self.cfg.capacity = max(self.cfg.capacity, capacity)
+
     def edges(self, out_ids, out_sims=None, stream=None) -> int:
         return knn_graph_get_edges(self.handle, out_ids, out_sims, stream)
 
@@ -461,13 +473,17 @@ class Server:
     owned by the server's worker until close(); submit() and wait() may be
     called from any thread (the C calls release the GIL)."""
 
-    def __init__(self, graph: "Graph", k_out: int, max_step_points: int = 0):
+    def __init__(self, graph: "Graph", k_out: int, max_step_points: int = 0,
+                 grow_headroom_bytes: int = 0):
+        """grow_headroom_bytes > 0: inserts beyond the graph's capacity grow
+        it while that many bytes of device memory stay free."""
         self.graph = graph
         self.k_out = k_out
         self.dim = graph.cfg.dim
         h = ctypes.c_void_p()
-        _check(lib.knn_server_create(graph.handle, ctypes.byref(KnnServerParams(k_out, max_step_points)),
-                                     ctypes.byref(h)), "knn_server_create")
+        params = KnnServerParams(k_out, max_step_points, grow_headroom_bytes)
+        _check(lib.knn_server_create(graph.handle, ctypes.byref(params), ctypes.byref(h)),
+               "knn_server_create")
         self.handle = h
 
     def submit(self, kind: int, vecs: np.ndarray) -> int:

@@ -68,3 +68,27 @@ def test_offchip_single_point_inserts(knn, clustered):
     mix, X, ids, sims = clustered
     og = oracle_graph(X, ids, sims, N + 16)
     single_point_inserts(knn, og, mix.sample(16, 5), 16.0, 5.0, 4, 2, 16, "off-chip seen sets")
+
+
+@pytest.fixture(scope="module")
+def clustered_d96():
+    """The precision workload's form off chip: d = 96, k = 20, 240,000 points
+    of a 120-component mixture, lists exact within each component."""
+    mix = Mixture(d=96, components=120, half_width=10.0, sigma=1.0, seed=62)
+    X, labels = mix.sample(N, 1, with_labels=True)
+    ids = np.full((N, 20), -1, np.int64)
+    for c in range(mix.components):
+        idx = np.flatnonzero(labels == c)
+        ci, _, _ = oracle.exact_knn(X[idx], 20)
+        ids[idx] = idx[ci]
+    return mix, X, ids
+
+
+@pytest.mark.parametrize("storage,amb", [(0, 11), (1, 24), (2, 41)])
+def test_offchip_queries_d96_k20(knn, clustered_d96, storage, amb):
+    """FP32 rows, and BF16 / FP8-E4M3 screening with the FP32 re-score of 4k
+    candidates; 48 queries, speedup 16.  The FP8 rows' wider rounding bound
+    flags most of these far-reaching searches as near ties."""
+    mix, X, ids = clustered_d96
+    compare(knn, X, mix.sample(48, 3), 20, 20, 16.0, 5.0, seed=4, storage=storage, o_ids=ids,
+            max_ambiguous=amb, label=f"off-chip d96 k20, storage {storage}")

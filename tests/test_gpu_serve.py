@@ -182,3 +182,76 @@ def test_capacity_refusal(knn):
             assert info["status"] == 0 and ids.shape == (5, K) and info["epoch"] == 1
     finally:
         g.close()
+
+
+def test_reserve_keeps_the_graph(knn):
+    """Growing a graph mid-stream (knn_graph_reserve) changes nothing the
+    method computes: the same inserts give the same lists as a graph created
+    with the larger capacity."""
+    pts = MIX.sample(300, 41)
+    lists = []
+    for grow in (False, True):
+        g = make_graph(knn, N0 + (100 if grow else 300))
+        try:
+            g.insert(cuda_tensor(pts[:100]))
+            if grow:
+                g.reserve(N0 + 300)
+                assert g.stats()["capacity"] == N0 + 300
+            g.insert(cuda_tensor(pts[100:200]))
+            g.insert(cuda_tensor(pts[200:]))
+            lists.append(edges(knn, g, N0 + 300))
+        finally:
+            g.close()
+    assert np.array_equal(lists[0], lists[1])
+
+
+def test_server_grows_the_graph_within_free_memory(knn):
+    """Admission by free device memory: with a headroom set, inserts beyond
+    the graph's capacity grow it (every request completes, ids stay dense,
+    the graph equals a replay of the steps on a graph sized for them from the
+    start); with a headroom larger than the device's memory no growth is
+    possible and such inserts fail with KNN_ERR_OOM while the rest go on."""
+    import torch
+    reqs = requests(80, seed=3)
+    n_ins = sum(p.shape[0] for k, p in reqs if k == 0)
+    g = make_graph(knn, N0 + 20)
+    try:
+        results = {}
+        with knn.Server(g, K, 256, grow_headroom_bytes=256 << 20) as srv:
+            rids = [(i, srv.submit(kind, pts)) for i, (kind, pts) in enumerate(reqs)]
+            for i, rid in rids:
+                kind, pts = reqs[i]
+                results[i] = srv.wait(rid, pts.shape[0], kind)
+            stats = srv.stats()
+        final = edges(knn, g, N0 + n_ins)
+    finally:
+        g.close()
+    assert all(r[2]["status"] == 0 for r in results.values())
+    assert stats["grows"] >= 1 and stats["capacity"] >= N0 + n_ins
+    new_ids = np.concatenate([results[i][0] for i, (k, _) in enumerate(reqs) if k == 0])
+    assert sorted(new_ids.tolist()) == list(range(N0, N0 + n_ins))
+    steps = {}
+    for i, (kind, _) in enumerate(reqs):
+        if kind == 0:
+            steps.setdefault(results[i][2]["step"], []).append(i)
+    g2 = make_graph(knn, N0 + n_ins)
+    try:
+        for st in sorted(steps):
+            g2.insert(cuda_tensor(np.concatenate([reqs[i][1] for i in sorted(steps[st])])))
+        assert np.array_equal(edges(knn, g2, N0 + n_ins), final)
+    finally:
+        g2.close()
+
+    free, total = torch.cuda.mem_get_info()
+    g = make_graph(knn, N0 + 10)
+    try:
+        with knn.Server(g, K, 64, grow_headroom_bytes=2 * total) as srv:
+            rid = srv.submit(0, MIX.sample(20, 5))
+            with pytest.raises(knn.KnnError) as exc:
+                srv.wait(rid, 20, 0)
+            assert exc.value.status == knn.KNN_ERR_OOM
+            ids, _, info = srv.wait(srv.submit(0, MIX.sample(10, 6)), 10, 0)
+            assert info["status"] == 0 and list(ids) == list(range(N0, N0 + 10))
+            assert srv.stats()["grows"] == 0
+    finally:
+        g.close()
