@@ -564,3 +564,24 @@ def test_partitioned_search_does_not_leave_its_part(orc):
                                             stream=11)
     assert tot["moves"] == 0 and tot["restarts"] == tot["evals"] == 25
     assert np.all(ids < 100)
+
+
+def test_sequential_recall_fixture_is_consistent(orc):
+    """tests/golden/sequential_recall_d128.txt (written by the oracle's
+    sequential build, Algorithm 1, on the d = 128 workload) against what its
+    own columns fix: recall = e_c / (n k) over all lists and over the
+    inserted ones, Q of Sec. 8.5 from e_c, and the mean search cost, which
+    the budget fixes exactly (every search of n nodes spends floor(n / 4)
+    similarities; n = 100,000 + i for insert i)."""
+    rows = [ln.split() for ln in read_golden("sequential_recall_d128.txt")]
+    assert [int(r[0]) for r in rows] == [13312, 20480, 25600, 100352]
+    n0, k = 100_000, 10
+    for r in rows:
+        c, n, e_all, e_new = (int(x) for x in r[:4])
+        rec, rec_new, q, s_ev, u_ev = (float(x) for x in r[4:])
+        assert n == n0 + c
+        assert rec == e_all / (n * k) and rec_new == e_new / (c * k)
+        assert abs(q - orc.quality_q(e_all, n0, c, k)) <= 1e-12
+        budget = sum((n0 + i) // 4 for i in range(c)) / c
+        assert s_ev == budget
+        assert 0 < u_ev <= k * k
