@@ -62,7 +62,7 @@ def parse_args():
                     help="store the initial points in the order of their balanced k-medoids "
                          "clusters (Algorithm 4; n/1000 clusters) before building the graph")
     ap.add_argument("--experiment", default=None,
-                    choices=("search", "depth", "partitions", "serving", "batching"),
+                    choices=("search", "depth", "partitions", "serving", "batching", "tail"),
                     help="instead of the benchmark line: the search sweeps (expansion e; "
                          "iGNNS against GNNS at equal evaluations) or the DEPTH sweep, "
                          "one JSON line per point")
@@ -832,6 +832,48 @@ def run_batching_experiment(knn, torch, np):
                   step_ms_p99=lat[-1], mean_items_per_step=items / len(lat), build_s=build_s)
 
 
+def run_tail_experiment(knn, torch, np):
+    """What bounds a search launch: per-insert counters of one 1,024-point
+    insert batch (every insert spends the same budget, but the dependent
+    climb steps and kept restarts vary widely), and the time of query
+    launches of 64, 256 and 1,024 queries -- a launch lasts as long as its
+    slowest search.  On the d = 128 workload (100,000 points, FP32) and the
+    precision workload (1,000,000 points, d = 96, k = 20, BF16 screening)."""
+    from paper_1602_06819_gb300 import inputs
+    names = ("search_evals", "update_evals", "restarts", "discarded", "moves", "adjacency_reads",
+             "draws")
+    for W, storage in ((inputs.PLAIN_D128, knn.KNN_STORAGE_FP32),
+                       (inputs.PRECISION_D96, knn.KNN_STORAGE_BF16)):
+        X0 = torch.from_numpy(W.initial()).cuda()
+        Xs = torch.from_numpy(W.mixture.sample(3 * W.batch, W.seed_stream)).cuda()
+        Q = torch.from_numpy(W.queries(1024)).cuda()
+        cfg = knn.GraphConfig(dim=W.mixture.d, k=W.k, depth=2, storage=storage, speedup=4.0,
+                              expansion=W.expansion, rescore_mult=4, max_batch=W.batch,
+                              seed=W.seed_search, capacity=W.n_init + 3 * W.batch)
+        g = knn.Graph(cfg, X0)
+        g.set_timing(True)
+        for i in range(3):
+            g.insert(Xs[i * W.batch:(i + 1) * W.batch])
+        search_ms = g.last_timing()["search"]
+        ctr = np.empty((W.batch, 8), np.int64)
+        g.counters(ctr)
+        pct = {nm: [int(np.percentile(ctr[:, c], p)) for p in (0, 50, 90, 99, 100)]
+               for c, nm in enumerate(names)}
+        pct["kept_restarts"] = [int(np.percentile(ctr[:, 2] - ctr[:, 3], p)) for p in (0, 50, 90, 99, 100)]
+        ids = torch.empty((1024, W.k), dtype=torch.int64, device="cuda")
+        launch_ms = {}
+        for m in (64, 256, 1024):
+            g.query(Q[:m], W.k, 0, ids[:m])
+            launch_ms[m] = g.last_timing()["search"]
+        g.close()
+        _exp_line(experiment="tail", workload=W.name, storage={0: "fp32", 1: "bf16"}[storage],
+                  n=W.n_init + 2 * W.batch,
+                  insert_batch_search_ms=search_ms, per_insert_percentiles_0_50_90_99_100=pct,
+                  query_launch_ms=launch_ms)
+        del X0, Xs, Q
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse_args()
     W = pick_workload(args)
@@ -847,7 +889,7 @@ def main():
         torch.cuda.set_device(0)
         {"search": run_search_experiment, "depth": run_depth_experiment,
          "partitions": run_partition_experiment, "serving": run_serving_experiment,
-         "batching": run_batching_experiment}[args.experiment](
+         "batching": run_batching_experiment, "tail": run_tail_experiment}[args.experiment](
             knn, torch, np)
         return
 
