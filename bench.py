@@ -688,7 +688,9 @@ def run_serving_experiment(knn, torch, np):
     rate lambda, about 15 s of traffic: completed points/s, p50/p99 request
     latency (submission to results on the host) and the mean step.  The same
     sweep on the plain FP32 path for comparison; recall@10 of 256 queries
-    against exhaustive search on the final graph of each run."""
+    against exhaustive search on the final graph of each run.  The graph is
+    created at its initial size and grows as inserts arrive (admission by
+    free device memory: knn_graph_reserve with 8 GiB kept free)."""
     from paper_1602_06819_gb300 import inputs
     import threading
     mix = inputs.Mixture(d=128, components=1000, half_width=20.0, sigma=1.0, seed=51)
@@ -699,11 +701,11 @@ def run_serving_experiment(knn, torch, np):
     for storage, lams in (("bf16", (10, 20, 30, 40, 60, 80)), ("fp32", (10, 20, 30, 40))):
         st = {"fp32": knn.KNN_STORAGE_FP32, "bf16": knn.KNN_STORAGE_BF16}[storage]
         cfg = knn.GraphConfig(dim=128, k=k, depth=2, storage=st, speedup=4.0, expansion=5.0,
-                              rescore_mult=4, max_batch=1024, seed=9, capacity=n0 + pool.shape[0])
+                              rescore_mult=4, max_batch=1024, seed=9, capacity=n0)
         g = knn.Graph(cfg, torch.from_numpy(mix.sample(n0, 50)).cuda())
         used = 0
         for lam in lams:
-            srv = knn.Server(g, k, 1024)
+            srv = knn.Server(g, k, 1024, grow_headroom_bytes=8 << 30)
             pending = []
             lock = threading.Lock()
             done_evt = threading.Event()
@@ -755,6 +757,7 @@ def run_serving_experiment(knn, torch, np):
                       p50_ms=lat[len(lat) // 2], p99_ms=lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                       steps=stats["steps"], mean_step_points=stats["points"] / max(1, stats["steps"]),
                       gpu_busy_frac=stats["busy_ms"] / (wall * 1e3), graph_n=g.stats()["n"],
+                      graph_capacity=stats["capacity"], grows=stats["grows"],
                       max_queue=stats["max_queue"], seconds=wall)
         # recall@10 of queries on the final graph against exhaustive search
         Q = torch.from_numpy(Qr).cuda()
@@ -812,6 +815,7 @@ def run_batching_experiment(knn, torch, np):
                              for r in tuned["tried"]])
         else:
             mg.set_launch(tuned["best"]["search_warps"])
+            mg.set_order(tuned["best"]["largest_first"])
         cap = tuned["best"]["step_cap"]
         for vecs, graph, kind, qids in steps[:3]:   # warm-up (and capture)
             mg.step_many(vecs, graph, kind, qids, cap)

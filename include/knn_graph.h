@@ -519,6 +519,14 @@ KNN_API knn_status knn_multi_step(knn_multi *mg, const float *vecs, const int32_
  * max_batch).  The search loops over the step's items with that many warps;
  * fewer than the items makes the launch persistent.  For the autotuner. */
 KNN_API knn_status knn_multi_set_launch(knn_multi *mg, int32_t search_warps);
+/* Order in which the search launch of later steps takes a step's items:
+ * largest_first = 0 as packed (inserts grouped by graph, then queries), 1
+ * the items of the largest graphs first.  A search's length grows with its
+ * graph's size (its budget is n / speedup), so with a persistent launch the
+ * longest searches then start in the first round instead of the last.  The
+ * results do not depend on it.  For the autotuner; KNN_ERR_INVALID_ARG for a
+ * value other than 0 or 1. */
+KNN_API knn_status knn_multi_set_order(knn_multi *mg, int32_t largest_first);
 /* Nodes and capacity of graph `graph`. */
 KNN_API knn_status knn_multi_graph_size(knn_multi *mg, int32_t graph, int64_t *n, int64_t *capacity);
 /* Lists of graph `graph`: out_ids [n, k] int64 local ids (host or device). */

@@ -1330,6 +1330,8 @@ struct knn_multi {
     int64_t *d_out = nullptr, *h_out = nullptr;
     float *d_sims = nullptr, *h_sims = nullptr;
     int32_t search_warps = 0;            // warps of the search launch (0: max_batch)
+    bool largest_first = false;          // search order of a step's items
+    int32_t *d_order = nullptr;          // [M] that order (step table)
     cudaGraphExec_t exec = nullptr;
     cudaStream_t exec_stream = nullptr;  // a CUDA graph is captured on and replayed from its own stream
     cudaEvent_t joined = nullptr;
@@ -1377,6 +1379,7 @@ static knn_status multi_launch(knn_multi *mg, cudaStream_t s) {
     a.vis_n = mg->cap_max;
     a.streams = mg->d_streams;
     a.seg = all;
+    a.seg.order = mg->d_order;
     CU(launch_search(g->p.storage, dp, a, s));
     const uint64_t *keys = g->keys_search;
     if (screening) {
@@ -1498,10 +1501,12 @@ KNN_API knn_status knn_multi_create(const knn_params *params, int32_t graphs, co
     knn_graph *g = mg->g;
     g->n = total;  // every slot is addressable; each graph's size is its own
     auto build = [&]() -> knn_status {
-        // step tables: counts[4] | item_seg[M] | lo[G] | n[G] | first[G+1] | perm[M] | streams[M]
+        // step tables: counts[4] | item_seg[M] | lo[G] | n[G] | first[G+1] | perm[M] | streams[M] |
+        // order[M]
         const size_t M = (size_t)mg->M, Gs = (size_t)graphs;
         mg->meta_bytes = align_up(16, 16) + align_up(M * 4, 16) + 2 * align_up(Gs * 4, 16) +
-                         align_up((Gs + 1) * 4, 16) + align_up(M * 4, 16) + align_up(M * 8, 16);
+                         align_up((Gs + 1) * 4, 16) + align_up(M * 4, 16) + align_up(M * 8, 16) +
+                         align_up(M * 4, 16);
         CU(cudaMallocHost(&mg->h_meta, mg->meta_bytes));
         CU(cudaMalloc(&mg->d_meta, mg->meta_bytes));
         size_t off = 0;
@@ -1517,6 +1522,7 @@ KNN_API knn_status knn_multi_create(const knn_params *params, int32_t graphs, co
         mg->d_first = (int32_t *)carve((Gs + 1) * 4);
         mg->d_perm = (int32_t *)carve(M * 4);
         mg->d_streams = (uint64_t *)carve(M * 8);
+        mg->d_order = (int32_t *)carve(M * 4);
         CU(cudaMallocHost(&mg->h_vecs, M * p.dim * 4));
         CU(cudaMalloc(&mg->d_vecs, M * p.dim * 4));
         CU(cudaMallocHost(&mg->h_out, M * p.k * 8));
@@ -1608,6 +1614,7 @@ KNN_API knn_status knn_multi_step(knn_multi *mg, const float *vecs, const int32_
     int32_t *first = (int32_t *)carve((Gs + 1) * 4);
     int32_t *perm = (int32_t *)carve(M * 4);
     uint64_t *streams = (uint64_t *)carve(M * 8);
+    int32_t *order = (int32_t *)carve(M * 4);
     first[0] = 0;
     for (int i = 0; i < G; ++i) {
         lo[i] = mg->lo[(size_t)i];
@@ -1629,6 +1636,15 @@ KNN_API knn_status knn_multi_step(knn_multi *mg, const float *vecs, const int32_
         item_seg[slot] = graph[i];
         perm[slot] = (int32_t)i;
         std::memcpy(mg->h_vecs + (size_t)slot * d, vecs + i * d, (size_t)d * 4);
+    }
+    // the order the search takes the items in: as packed, or the items of the
+    // largest graphs first (a search's length grows with its graph, so the
+    // longest ones start in the first round of a persistent launch)
+    for (int32_t i = 0; i < (int32_t)m; ++i) order[i] = i;
+    if (mg->largest_first) {
+        std::stable_sort(order, order + m, [&](int32_t x, int32_t y) {
+            return mg->n[(size_t)item_seg[x]] > mg->n[(size_t)item_seg[y]];
+        });
     }
     counts[0] = (int32_t)m;
     counts[1] = (int32_t)m_ins;
@@ -1678,6 +1694,12 @@ KNN_API knn_status knn_multi_step(knn_multi *mg, const float *vecs, const int32_
     g->queries += m - m_ins;
     g->last_m = m;
     ++mg->steps;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_multi_set_order(knn_multi *mg, int32_t largest_first) {
+    if (!mg || (largest_first != 0 && largest_first != 1)) return fail(KNN_ERR_INVALID_ARG, "bad argument");
+    mg->largest_first = largest_first != 0;
     return KNN_OK;
 }
 

@@ -53,6 +53,7 @@ struct Segments {
     const uint32_t *n = nullptr;         // [S] nodes before the step
     const int32_t *first = nullptr;      // [S + 1] insert items of each graph
     const int32_t *count = nullptr;      // device item count of the launch
+    const int32_t *order = nullptr;      // nullable: [items] the order the search takes them in
 };
 
 __host__ __device__ __forceinline__ uint32_t seg_new_id(const Segments &sg, int32_t s, int32_t item) {

@@ -132,7 +132,10 @@ ignns_search_kernel(const SearchArgs a) {
     // search sw: query sw / parts over partition sw % parts, the nodes
     // lo .. lo + np - 1 (one partition: every node); with several graphs,
     // item sw over its graph's nodes
-    for (int sw = blockIdx.x * SEARCH_WARPS + wib; sw < nsearch; sw += nwarps) {
+    for (int si = blockIdx.x * SEARCH_WARPS + wib; si < nsearch; si += nwarps) {
+        // several graphs: the step's tables may give the order the warps take
+        // the items in (a search's result does not depend on when it runs)
+        const int sw = (multi && a.seg.order) ? a.seg.order[si] : si;
         const int qi = multi ? sw : sw / a.parts, part = multi ? 0 : sw % a.parts;
         uint32_t lo = 0u, np = a.n;
         int64_t live = a.n_live, budget = a.budget;

@@ -53,7 +53,7 @@ EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "
             "knn_exact_set_wait_limit",
             "knn_balanced_kmedoids", "knn_server_create", "knn_server_submit", "knn_server_wait",
             "knn_server_get_stats", "knn_server_destroy", "knn_multi_create", "knn_multi_step",
-            "knn_multi_set_launch", "knn_multi_graph_size", "knn_multi_get_edges", "knn_multi_destroy",
+            "knn_multi_set_launch", "knn_multi_set_order", "knn_multi_graph_size", "knn_multi_get_edges", "knn_multi_destroy",
             "knn_search_noalloc",
             "knn_last_error", "knn_version")
 
@@ -150,6 +150,7 @@ def _load_library() -> ctypes.CDLL:
         "knn_multi_create": (I32, [ctypes.POINTER(KnnParams), I32, P, P, P, I32, P, ctypes.POINTER(P)]),
         "knn_multi_step": (I32, [P, P, P, P, P, I64, P, P, P]),
         "knn_multi_set_launch": (I32, [P, I32]),
+        "knn_multi_set_order": (I32, [P, I32]),
         "knn_multi_graph_size": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "knn_multi_get_edges": (I32, [P, I32, P, P]),
         "knn_multi_destroy": (None, [P]),
@@ -555,32 +556,40 @@ class MultiGraph:
     def set_launch(self, search_warps: int):
         _check(lib.knn_multi_set_launch(self.handle, search_warps), "knn_multi_set_launch")
 
+    def set_order(self, largest_first: bool):
+        _check(lib.knn_multi_set_order(self.handle, int(bool(largest_first))), "knn_multi_set_order")
+
     def autotune(self, sample, step_caps=(512, 1024, 2048, 4096), warps=(608, 1216, 2432, 0),
-                 repeats: int = 2) -> dict:
-        """Pick the search launch width and the step size cap by timing
-        query-only steps of `sample` (vecs, graph, query_ids: read-only, so
-        the graphs do not change).  Returns the chosen settings and the times
-        measured; the chosen launch width is set, the step cap is returned for
-        the caller's batching (step_many)."""
+                 orders=(False, True), repeats: int = 2) -> dict:
+        """Pick the search launch width, the order the search takes a step's
+        items in (as packed, or the largest graphs first) and the step size
+        cap by timing query-only steps of `sample` (vecs, graph, query_ids:
+        read-only, so the graphs do not change).  Returns the chosen settings
+        and the times measured; the chosen width and order are set, the step
+        cap is returned for the caller's batching (step_many)."""
         import time
         vecs, graph, qids = sample
         kind = np.ones(len(graph), np.int32)
         best, table = None, []
         for w in warps:
             self.set_launch(w)
-            for cap in step_caps:
-                if cap > self.cfg.max_batch:
-                    continue
-                self.step_many(vecs[:cap], graph[:cap], kind[:cap], qids[:cap], cap)  # warm (and capture)
-                t0 = time.perf_counter()
-                for _ in range(repeats):
-                    self.step_many(vecs, graph, kind, qids, cap)
-                dt = (time.perf_counter() - t0) / repeats
-                rate = len(graph) / dt
-                table.append({"search_warps": w, "step_cap": cap, "items_per_s": rate})
-                if best is None or rate > best["items_per_s"]:
-                    best = table[-1]
+            for lf in orders:
+                self.set_order(lf)
+                for cap in step_caps:
+                    if cap > self.cfg.max_batch:
+                        continue
+                    self.step_many(vecs[:cap], graph[:cap], kind[:cap], qids[:cap], cap)  # warm (and capture)
+                    t0 = time.perf_counter()
+                    for _ in range(repeats):
+                        self.step_many(vecs, graph, kind, qids, cap)
+                    dt = (time.perf_counter() - t0) / repeats
+                    rate = len(graph) / dt
+                    table.append({"search_warps": w, "largest_first": bool(lf), "step_cap": cap,
+                                  "items_per_s": rate})
+                    if best is None or rate > best["items_per_s"]:
+                        best = table[-1]
         self.set_launch(best["search_warps"])
+        self.set_order(best["largest_first"])
         return {"best": best, "tried": table}
 
     def step_many(self, vecs, graph, kind, query_ids, cap: int):

@@ -3,7 +3,8 @@ queries over graphs of uneven sizes must leave every graph exactly as a
 knn_graph given the same items would -- query results (ids and
 similarities), new ids and final lists bit-identical -- with the launch
 sequence run directly and replayed from a CUDA graph, for FP32 and for BF16
-screening."""
+screening, with one warp per item and with a persistent search launch that
+takes the items of the largest graphs first."""
 import numpy as np
 import pytest
 
@@ -45,14 +46,18 @@ def steps(mixes, n_steps, seed):
     return out
 
 
-@pytest.mark.parametrize("storage,use_graph", [(0, True), (0, False), (1, True)])
-def test_multi_graph_step_equals_single_graphs(knn, storage, use_graph):
+@pytest.mark.parametrize("storage,use_graph,largest_first,warps", [
+    (0, True, False, 0), (0, False, False, 0), (1, True, False, 0),
+    (0, True, True, 64), (1, False, True, 64)])   # persistent searches, largest graphs first
+def test_multi_graph_step_equals_single_graphs(knn, storage, use_graph, largest_first, warps):
     import torch
     mixes = mixtures()
     inits = [mixes[i].sample(SIZES[i], 1) for i in range(len(SIZES))]
     cfg = knn.GraphConfig(dim=D, k=K, depth=2, storage=storage, speedup=4.0, expansion=5.0,
                           rescore_mult=4, max_batch=256, seed=7)
     mg = knn.MultiGraph(cfg, SIZES, CAPS, cuda_tensor(np.concatenate(inits)), use_graph=use_graph)
+    mg.set_launch(warps)
+    mg.set_order(largest_first)
     singles = []
     for i in range(len(SIZES)):
         c = knn.GraphConfig(dim=D, k=K, depth=2, storage=storage, speedup=4.0, expansion=5.0,
