@@ -698,14 +698,30 @@ def run_serving_experiment(knn, torch, np):
     pool = mix.sample(600_000, 52)
     Qr = mix.sample(256, 53)
     rng = np.random.default_rng(54)
-    for storage, lams in (("bf16", (10, 20, 30, 40, 60, 80)), ("fp32", (10, 20, 30, 40))):
+    for storage, lams, parts in (("bf16", (10, 20, 30, 40, 60, 80), 0), ("fp32", (10, 20, 30, 40), 0),
+                                 ("bf16", (10, 20, 30), 32)):
         st = {"fp32": knn.KNN_STORAGE_FP32, "bf16": knn.KNN_STORAGE_BF16}[storage]
         cfg = knn.GraphConfig(dim=128, k=k, depth=2, storage=st, speedup=4.0, expansion=5.0,
                               rescore_mult=4, max_batch=1024, seed=9, capacity=n0)
-        g = knn.Graph(cfg, torch.from_numpy(mix.sample(n0, 50)).cuda())
+        X0 = torch.from_numpy(mix.sample(n0, 50)).cuda()
+        offs = None
+        if parts:
+            # queries run the partitioned search (Algorithm 3) over the balanced
+            # k-medoids clusters of the initial points, stored cluster by cluster
+            perm = torch.empty(n0, dtype=torch.int64, device="cuda")
+            offs_d = torch.empty(parts + 1, dtype=torch.int64, device="cuda")
+            knn.knn_balanced_kmedoids(X0, parts, 1.05, 1, 2, 5, order=perm, offsets=offs_d)
+            X0 = X0[perm].contiguous()
+            offs = offs_d.cpu().numpy()
+        g = knn.Graph(cfg, X0)
+        del X0
         used = 0
         for lam in lams:
-            srv = knn.Server(g, k, 1024, grow_headroom_bytes=8 << 30)
+            o = None
+            if parts:   # the parts of the graph as it stands (the last one takes the inserts)
+                o = offs.copy()
+                o[-1] = g.stats()["n"]
+            srv = knn.Server(g, k, 1024, grow_headroom_bytes=8 << 30, part_offsets=o)
             pending = []
             lock = threading.Lock()
             done_evt = threading.Event()
@@ -752,7 +768,7 @@ def run_serving_experiment(knn, torch, np):
             stats = srv.stats()
             srv.close()
             lat.sort()
-            _exp_line(experiment="serving", storage=storage, lam_requests_per_s=lam, requests=nsub,
+            _exp_line(experiment="serving", storage=storage, query_parts=parts, lam_requests_per_s=lam, requests=nsub,
                       points_per_s=sum(sizes) / wall, offered_points_per_s=lam * 256.5,
                       p50_ms=lat[len(lat) // 2], p99_ms=lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                       steps=stats["steps"], mean_step_points=stats["points"] / max(1, stats["steps"]),
@@ -762,13 +778,19 @@ def run_serving_experiment(knn, torch, np):
         # recall@10 of queries on the final graph against exhaustive search
         Q = torch.from_numpy(Qr).cuda()
         ids = torch.empty((256, k), dtype=torch.int64, device="cuda")
-        g.query(Q, k, 0, ids)
+        if parts:
+            fo = offs.copy()
+            fo[-1] = g.stats()["n"]
+            g.query_partitioned(Q, k, 0, torch.from_numpy(fo), ids)
+        else:
+            g.query(Q, k, 0, ids)
         got = ids.clone()
         g.set_search(1.0, math.inf, "eager")
         g.query(Q, k, 0, ids)
         torch.cuda.synchronize()
         rec = float((got[:, :, None] == ids[:, None, :]).any(-1).float().mean().item())
-        _exp_line(experiment="serving_recall", storage=storage, graph_n=g.stats()["n"], recall_at_10=rec)
+        _exp_line(experiment="serving_recall", storage=storage, query_parts=parts, graph_n=g.stats()["n"],
+                  recall_at_10=rec)
         g.close()
 
 

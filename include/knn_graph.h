@@ -206,6 +206,18 @@ KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, 
                                                void *stream);
 
 /*
+ * knn_graph_query_partitioned with one restart stream per query, as
+ * knn_graph_query_ids: query i of partition j uses stream
+ * 2^63 + query_ids[i] + j * 2^56 (query_ids: [m] uint64, host or device), so
+ * a query's result depends only on the graph, its vector, its id and the
+ * partitions -- the form the continuous-batching server uses.
+ */
+KNN_API knn_status knn_graph_query_partitioned_ids(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                                   const uint64_t *query_ids, const int64_t *part_offsets,
+                                                   int32_t parts, int64_t *out_ids, float *out_sims,
+                                                   void *stream);
+
+/*
  * Remove m nodes (not in the paper).  Removed nodes are never drawn, climbed
  * to, returned or offered again; lists that still hold them keep the entry.
  * KNN_ERR_NOT_FOUND if an id is outside 0 .. n-1.  ids: [m] int64.
@@ -434,6 +446,16 @@ typedef struct knn_server_params {
                                     insert that cannot be admitted so fails with
                                     KNN_ERR_OOM.  0: the capacity is fixed and
                                     such an insert fails with KNN_ERR_CAPACITY    */
+    int32_t query_parts;     /* > 1: queries run the partitioned search
+                                (knn_graph_query_partitioned_ids) over the parts
+                                given by part_offsets, the last part stretched to
+                                the nodes inserted since; a query's result is then
+                                a function of (epoch, vector, request, point,
+                                parts).  0 or 1: the plain search            */
+    int32_t reserved;        /* 0                                                    */
+    const int64_t *part_offsets; /* [query_parts + 1] host int64 node offsets of
+                                    the graph at server creation, nondecreasing
+                                    from 0 to its n (copied at creation)        */
 } knn_server_params;
 
 typedef enum knn_request_kind { KNN_REQ_INSERT = 0, KNN_REQ_QUERY = 1 } knn_request_kind;

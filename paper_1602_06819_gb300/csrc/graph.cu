@@ -906,10 +906,11 @@ KNN_API knn_status knn_graph_query_ids(knn_graph *g, const float *vecs, int64_t 
     return KNN_OK;
 }
 
-KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
-                                               uint64_t query_id0, const int64_t *part_offsets, int32_t parts,
-                                               int64_t *out_ids, float *out_sims, void *stream) {
-    NvtxRange nvtx_range("knn_graph_query_partitioned");
+// Partitioned queries; query i uses restart stream 2^63 + query_id0 + i, or
+// 2^63 + query_ids[i] when query_ids is given.
+static knn_status query_partitioned(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                    uint64_t query_id0, const uint64_t *query_ids, const int64_t *part_offsets,
+                                    int32_t parts, int64_t *out_ids, float *out_sims, void *stream) {
     if (!g || !vecs || !out_ids || !part_offsets) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 1 || m > g->p.max_batch)
         return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
@@ -934,8 +935,9 @@ KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, 
     for (int q = 0; q < parts; ++q) {
         if (off[(size_t)q + 1] < off[(size_t)q]) return fail(KNN_ERR_INVALID_ARG, "partition offsets decrease");
         int64_t rem = 0;
-        for (int64_t v = off[(size_t)q]; v < off[(size_t)q + 1]; ++v)
-            rem += (g->removed_host[(size_t)(v >> 5)] >> (v & 31)) & 1u;
+        if (g->n_removed > 0)
+            for (int64_t v = off[(size_t)q]; v < off[(size_t)q + 1]; ++v)
+                rem += (g->removed_host[(size_t)(v >> 5)] >> (v & 31)) & 1u;
         live[(size_t)q] = off[(size_t)q + 1] - off[(size_t)q] - rem;
         largest = std::max(largest, off[(size_t)q + 1] - off[(size_t)q]);
     }
@@ -944,6 +946,11 @@ KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, 
     phase_begin_call(g);
     phase_mark(g, KNN_PHASE_STORE, s);
     TRY(append_rows(g, vecs, m, 0, g->qbuf, false, s));
+    if (query_ids) {
+        CU(cudaMemcpyAsync(g->qstreams, query_ids, (size_t)m * 8, cudaMemcpyDefault, s));
+        CU(launch_add_u64(g->qstreams, 1ull << 63, m, s));
+        ++g->launches;
+    }
     g->phase_ran[KNN_PHASE_STORE] = true;
     phase_mark(g, KNN_PHASE_SEARCH, s);
     const bool screening = g->p.storage != KNN_STORAGE_FP32;
@@ -977,6 +984,7 @@ KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, 
         a.max_draws = 64ull * (uint64_t)g->n;
         a.seed = g->p.seed;
         a.stream_base = (1ull << 63) + query_id0 + (uint64_t)q0;
+        a.streams = query_ids ? g->qstreams + q0 : nullptr;
         const double e = g->p.expansion;
         a.discard = (e > 0.0 && std::isfinite(e)) ? 1 : 0;
         a.expansion = a.discard ? (float)e : 1.0f;
@@ -1017,6 +1025,23 @@ KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, 
     g->queries += m;
     g->last_m = m;
     return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_query_partitioned(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                               uint64_t query_id0, const int64_t *part_offsets, int32_t parts,
+                                               int64_t *out_ids, float *out_sims, void *stream) {
+    NvtxRange nvtx_range("knn_graph_query_partitioned");
+    return query_partitioned(g, vecs, m, k_out, query_id0, nullptr, part_offsets, parts, out_ids, out_sims,
+                             stream);
+}
+
+KNN_API knn_status knn_graph_query_partitioned_ids(knn_graph *g, const float *vecs, int64_t m, int32_t k_out,
+                                                   const uint64_t *query_ids, const int64_t *part_offsets,
+                                                   int32_t parts, int64_t *out_ids, float *out_sims,
+                                                   void *stream) {
+    NvtxRange nvtx_range("knn_graph_query_partitioned_ids");
+    if (!query_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    return query_partitioned(g, vecs, m, k_out, 0, query_ids, part_offsets, parts, out_ids, out_sims, stream);
 }
 
 KNN_API knn_status knn_graph_remove(knn_graph *g, const int64_t *ids, int64_t m, void *stream) {

@@ -92,6 +92,7 @@ struct knn_server {
     bool stopping = false;
     int64_t pending_inserts = 0;  // insert points admitted into the step being formed
     int64_t headroom = 0;         // bytes that must stay free when the graph grows (0: no growth)
+    std::vector<int64_t> parts;   // query partitions at creation (empty: plain search)
     bool grow_failed = false;     // the last growth for the insert at the queue head failed
     knn_server_stats stats{};
     std::thread worker;
@@ -234,8 +235,17 @@ void knn_server::run() {
                 return server_fail(KNN_ERR_CUDA, "server upload failed");
             cudaEventRecord(sl.t0, comp);
             if (sl.mq > 0) {
-                const knn_status st = knn_graph_query_ids(g, sl.d_vecs, sl.mq, k_out, sl.d_qids, sl.d_qids_out,
-                                                          sl.d_sims, comp);
+                knn_status st;
+                if (parts.empty()) {
+                    st = knn_graph_query_ids(g, sl.d_vecs, sl.mq, k_out, sl.d_qids, sl.d_qids_out, sl.d_sims, comp);
+                } else {
+                    // the parts at creation, the last one stretched over the
+                    // nodes inserted since (the graph of this step's epoch)
+                    std::vector<int64_t> off(parts);
+                    off.back() = shape.n;
+                    st = knn_graph_query_partitioned_ids(g, sl.d_vecs, sl.mq, k_out, sl.d_qids, off.data(),
+                                                         (int32_t)off.size() - 1, sl.d_qids_out, sl.d_sims, comp);
+                }
                 if (st != KNN_OK) return st;
             }
             if (sl.mi > 0) {
@@ -290,6 +300,16 @@ KNN_API knn_status knn_server_create(knn_graph *g, const knn_server_params *p, k
     s->P = P;
     if (p->grow_headroom_bytes < 0) return server_fail(KNN_ERR_INVALID_ARG, "grow_headroom_bytes must be >= 0");
     s->headroom = p->grow_headroom_bytes;
+    if (p->query_parts > 1) {
+        if (!p->part_offsets || p->query_parts > KNN_MAX_PARTS || p->query_parts > sh.max_batch)
+            return server_fail(KNN_ERR_INVALID_ARG, "query_parts needs part_offsets and at most KNN_MAX_PARTS parts");
+        s->parts.assign(p->part_offsets, p->part_offsets + p->query_parts + 1);
+        if (s->parts.front() != 0 || s->parts.back() != sh.n)
+            return server_fail(KNN_ERR_INVALID_ARG, "part_offsets must run from 0 to the graph's n");
+        for (int q = 0; q < p->query_parts; ++q)
+            if (s->parts[(size_t)q + 1] < s->parts[(size_t)q])
+                return server_fail(KNN_ERR_INVALID_ARG, "part_offsets decrease");
+    }
     s->stats.capacity = sh.capacity;
     if (cudaGetDevice(&s->device) != cudaSuccess) return server_fail(KNN_ERR_CUDA, "no CUDA device");
     bool ok = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking) == cudaSuccess &&

@@ -45,7 +45,8 @@ COUNTER_NAMES = ("search_evals", "update_evals", "restarts", "discarded", "moves
 
 # Every symbol include/knn_graph.h declares.
 EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "knn_graph_query_batch",
-            "knn_graph_query_ids", "knn_graph_query_partitioned", "knn_graph_remove", "knn_graph_get_edges",
+            "knn_graph_query_ids", "knn_graph_query_partitioned", "knn_graph_query_partitioned_ids",
+            "knn_graph_remove", "knn_graph_get_edges",
             "knn_graph_reserve",
             "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
@@ -90,7 +91,8 @@ class KnnExactInfo(ctypes.Structure):
 
 class KnnServerParams(ctypes.Structure):
     _fields_ = [("k_out", ctypes.c_int32), ("max_step_points", ctypes.c_int32),
-                ("grow_headroom_bytes", ctypes.c_int64)]
+                ("grow_headroom_bytes", ctypes.c_int64), ("query_parts", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("part_offsets", ctypes.c_void_p)]
 
 
 class KnnRequestInfo(ctypes.Structure):
@@ -131,6 +133,7 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_query_batch": (I32, [P, P, I64, I32, U64, P, P, P]),
         "knn_graph_query_partitioned": (I32, [P, P, I64, I32, U64, P, I32, P, P, P]),
         "knn_graph_query_ids": (I32, [P, P, I64, I32, P, P, P, P]),
+        "knn_graph_query_partitioned_ids": (I32, [P, P, I64, I32, P, P, I32, P, P, P]),
         "knn_graph_remove": (I32, [P, P, I64, P]),
         "knn_graph_reserve": (I32, [P, I64, I64, P]),
         "knn_graph_get_edges": (I32, [P, P, P, I64, ctypes.POINTER(I64), P]),
@@ -266,6 +269,19 @@ def knn_graph_query_partitioned(g, vecs, k_out: int, query_id0: int, part_offset
                                            _ptr(part_offsets), part_offsets.shape[0] - 1,
                                            _ptr(out_ids), _ptr(out_sims), _stream(stream)),
            "knn_graph_query_partitioned")
+
+
+def knn_graph_query_partitioned_ids(g, vecs, k_out: int, query_ids, part_offsets, out_ids,
+                                    out_sims=None, stream=None) -> None:
+    """Algorithm 3 with one restart stream per query (2^63 + query_ids[i])."""
+    _check_dtype(vecs, "float32", "vecs")
+    _check_dtype(part_offsets, "int64", "part_offsets")
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_sims, "float32", "out_sims")
+    _check(lib.knn_graph_query_partitioned_ids(g, _ptr(vecs), vecs.shape[0], k_out, _ptr(query_ids),
+                                               _ptr(part_offsets), part_offsets.shape[0] - 1,
+                                               _ptr(out_ids), _ptr(out_sims), _stream(stream)),
+           "knn_graph_query_partitioned_ids")
 
 
 def knn_graph_remove(g, ids, stream=None) -> None:
@@ -418,6 +434,10 @@ class Graph:
     def query(self, vecs, k_out, query_id0, out_ids, out_sims=None, stream=None):
         knn_graph_query_batch(self.handle, vecs, k_out, query_id0, out_ids, out_sims, stream)
 
+    def query_partitioned_ids(self, vecs, k_out, query_ids, part_offsets, out_ids, out_sims=None, stream=None):
+        knn_graph_query_partitioned_ids(self.handle, vecs, k_out, query_ids, part_offsets, out_ids, out_sims,
+                                        stream)
+
     def query_ids(self, vecs, k_out, query_ids, out_ids, out_sims=None, stream=None):
         knn_graph_query_ids(self.handle, vecs, k_out, query_ids, out_ids, out_sims, stream)
 
@@ -475,14 +495,19 @@ class Server:
     called from any thread (the C calls release the GIL)."""
 
     def __init__(self, graph: "Graph", k_out: int, max_step_points: int = 0,
-                 grow_headroom_bytes: int = 0):
+                 grow_headroom_bytes: int = 0, part_offsets=None):
         """grow_headroom_bytes > 0: inserts beyond the graph's capacity grow
-        it while that many bytes of device memory stay free."""
+        it while that many bytes of device memory stay free.  part_offsets
+        (host int64 [parts + 1], 0 .. the graph's n): queries run the
+        partitioned search over those node ranges."""
         self.graph = graph
         self.k_out = k_out
         self.dim = graph.cfg.dim
         h = ctypes.c_void_p()
-        params = KnnServerParams(k_out, max_step_points, grow_headroom_bytes)
+        offs = None if part_offsets is None else np.ascontiguousarray(part_offsets, dtype=np.int64)
+        params = KnnServerParams(k_out, max_step_points, grow_headroom_bytes,
+                                 0 if offs is None else offs.shape[0] - 1, 0,
+                                 None if offs is None else offs.ctypes.data)
         _check(lib.knn_server_create(graph.handle, ctypes.byref(params), ctypes.byref(h)),
                "knn_server_create")
         self.handle = h

@@ -51,11 +51,11 @@ def edges(knn, g, n):
     return e.cpu().numpy()
 
 
-def serve(knn, g, reqs, threads=4, max_step=256):
+def serve(knn, g, reqs, threads=4, max_step=256, part_offsets=None):
     """Submit from several client threads, each waiting on its own requests."""
     results = {}
     lock = threading.Lock()
-    with knn.Server(g, K, max_step) as srv:
+    with knn.Server(g, K, max_step, part_offsets=part_offsets) as srv:
         def client(part):
             mine = []
             for idx in part:
@@ -255,3 +255,54 @@ def test_server_grows_the_graph_within_free_memory(knn):
             assert srv.stats()["grows"] == 0
     finally:
         g.close()
+
+
+def test_partitioned_queries_alone_match_the_mix(knn):
+    """A server whose queries run the partitioned search (Algorithm 3) over
+    three node ranges of the initial graph, the last one stretched over the
+    nodes inserted since: every query replayed alone
+    (knn_graph_query_partitioned_ids) against the graph of its recorded
+    epoch, with the parts of that epoch, returns exactly what it returned in
+    the mix."""
+    import torch
+    reqs = requests(100, seed=5)
+    n_ins = sum(p.shape[0] for k, p in reqs if k == 0)
+    offs = np.array([0, 1000, 2000, N0], np.int64)
+    g = make_graph(knn, N0 + n_ins)
+    try:
+        results, stats = serve(knn, g, reqs, part_offsets=offs)
+    finally:
+        g.close()
+    assert all(r[3]["status"] == 0 for r in results.values())
+    steps = {}
+    for idx in range(len(reqs)):
+        steps.setdefault(results[idx][3]["step"], []).append(idx)
+    g2 = make_graph(knn, N0 + n_ins)
+    try:
+        n = N0
+        compared = 0
+        for st in sorted(steps):
+            members = sorted(steps[st], key=lambda i: results[i][0])
+            for idx in members:
+                kind, pts = reqs[idx]
+                if kind != 1:
+                    continue
+                rid = results[idx][0]
+                m = pts.shape[0]
+                qids = torch.tensor([(rid << 20) + i for i in range(m)], dtype=torch.int64)
+                out = torch.empty((m, K), dtype=torch.int64, device="cuda")
+                outs = torch.empty((m, K), dtype=torch.float32, device="cuda")
+                epoch_offs = offs.copy()
+                epoch_offs[-1] = n
+                g2.query_partitioned_ids(cuda_tensor(pts), K, qids, torch.from_numpy(epoch_offs), out, outs)
+                torch.cuda.synchronize()
+                assert np.array_equal(out.cpu().numpy(), results[idx][1]), f"request {rid}"
+                assert np.array_equal(outs.cpu().numpy(), results[idx][2])
+                compared += 1
+            ins = [reqs[idx][1] for idx in members if reqs[idx][0] == 0]
+            if ins:
+                g2.insert(cuda_tensor(np.concatenate(ins)))
+                n += sum(p.shape[0] for p in ins)
+        assert compared == sum(1 for k, _ in reqs if k == 1)
+    finally:
+        g2.close()
