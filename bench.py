@@ -62,7 +62,7 @@ def parse_args():
                     help="store the initial points in the order of their balanced k-medoids "
                          "clusters (Algorithm 4; n/1000 clusters) before building the graph")
     ap.add_argument("--experiment", default=None,
-                    choices=("search", "depth", "partitions", "serving", "batching", "tail"),
+                    choices=("search", "depth", "partitions", "serving", "batching", "tail", "growth"),
                     help="instead of the benchmark line: the search sweeps (expansion e; "
                          "iGNNS against GNNS at equal evaluations) or the DEPTH sweep, "
                          "one JSON line per point")
@@ -794,6 +794,66 @@ def run_serving_experiment(knn, torch, np):
         g.close()
 
 
+def run_growth_experiment(knn, torch, np):
+    """The serving pattern's growth: one graph of 1,000,000 points (d = 128,
+    1,000 components, k = 10, BF16 screening with FP32 re-score, speedup 4,
+    e = 5) created at exactly that size and grown to 5,000,000 through the
+    continuous-batching server, which admits inserts by free device memory
+    (knn_graph_reserve whenever an insert does not fit, keeping 8 GiB free).
+    Insert requests of 512 points are submitted as fast as the server takes
+    them, with a 1-point query request every 20th request; every 200,000
+    nodes a line reports the graph's size and capacity, the growth steps so
+    far, the insert rate of that stretch and the latency of its queries."""
+    from paper_1602_06819_gb300 import inputs
+    mix = inputs.Mixture(d=128, components=1000, half_width=20.0, sigma=1.0, seed=51)
+    n0, n_end, k, req = 1_000_000, 5_000_000, 10, 512
+    cfg = knn.GraphConfig(dim=128, k=k, depth=2, storage=knn.KNN_STORAGE_BF16, speedup=4.0,
+                          expansion=5.0, rescore_mult=4, max_batch=1024, seed=9, capacity=n0)
+    g = knn.Graph(cfg, torch.from_numpy(mix.sample(n0, 50)).cuda())
+    pool = mix.sample(400_000, 55)
+    rng = np.random.default_rng(56)
+    srv = knn.Server(g, k, 1024, grow_headroom_bytes=8 << 30)
+    n, used, nreq = n0, 0, 0
+    inflight = []
+    mark, t_mark, q_lat = n0, time.perf_counter(), []
+    t_start = t_mark
+    while n < n_end and time.perf_counter() - t_start < 1800.0:   # at most half an hour
+        while len(inflight) < 8:
+            if nreq % 20 == 19:
+                q = mix.sample(1, 1_000_000 + nreq)
+                inflight.append((srv.submit(knn.KNN_REQ_QUERY, q), 1, knn.KNN_REQ_QUERY))
+            else:
+                if used + req > pool.shape[0]:
+                    used = 0
+                inflight.append((srv.submit(knn.KNN_REQ_INSERT, pool[used:used + req]), req,
+                                 knn.KNN_REQ_INSERT))
+                used += req
+            nreq += 1
+        rid, m, kind = inflight.pop(0)
+        _, _, info = srv.wait(rid, m, kind)
+        if kind == knn.KNN_REQ_INSERT:
+            n += m
+        else:
+            q_lat.append(info["latency_ms"])
+        if n - mark >= 200_000 or n >= n_end:
+            now = time.perf_counter()
+            st = srv.stats()
+            q_lat.sort()
+            _exp_line(experiment="growth", n=n, capacity=st["capacity"], grows=st["grows"],
+                      inserts_per_s=(n - mark) / (now - t_mark),
+                      query_latency_ms_p50=q_lat[len(q_lat) // 2] if q_lat else None,
+                      query_latency_ms_max=q_lat[-1] if q_lat else None,
+                      seconds=now - t_start)
+            mark, t_mark, q_lat = n, now, []
+    for rid, m, kind in inflight:
+        srv.wait(rid, m, kind)
+    srv.close()
+    st = g.stats()
+    _exp_line(experiment="growth_end", n=st["n"], capacity=st["capacity"], device_bytes=st["device_bytes"],
+              seconds=time.perf_counter() - t_start)
+    g.close()
+
+
 def run_batching_experiment(knn, torch, np):
     """The batching pattern: 64 independent graphs of uneven sizes (n
     log-uniform in 1,000 .. 200,000, d = 64 FP32, k = 10, each its own
@@ -915,7 +975,8 @@ def main():
         torch.cuda.set_device(0)
         {"search": run_search_experiment, "depth": run_depth_experiment,
          "partitions": run_partition_experiment, "serving": run_serving_experiment,
-         "batching": run_batching_experiment, "tail": run_tail_experiment}[args.experiment](
+         "batching": run_batching_experiment, "tail": run_tail_experiment,
+         "growth": run_growth_experiment}[args.experiment](
             knn, torch, np)
         return
 

@@ -11,7 +11,9 @@
 //   warp 0      TMA: the CTA's rows (hi and lo) once, then the column tiles,
 //               one 64-element K slice (hi and lo) per ring stage;
 //   warp 1      owns the TMEM allocation; one thread issues the MMAs of a
-//               128-column tile into one of two FP32 accumulators;
+//               128-column tile into one of four FP32 accumulators (all
+//               512 TMEM columns), so it can run three tiles ahead of the
+//               epilogue;
 //   warp 2      copies each tile's column norms beside its accumulator;
 //   warps 4..11 epilogue, two warpgroups: thread r of warpgroup h reads
 //               accumulator lane r (its row), columns 64h .. 64h+63 of each
@@ -49,10 +51,11 @@ using namespace tc;
 
 constexpr int TC_ROWS = 128;            // rows per CTA (MMA M)
 constexpr int TC_COLS = 128;            // columns per tile (MMA N)
+constexpr int TC_NACC = 4;              // TMEM accumulators (all 512 columns): the MMAs run ahead by up to 3 tiles
 constexpr int TC_CAND = 32;             // candidates kept per row and warpgroup
 constexpr int TC_NCAND = 2 * TC_CAND;   // candidates per row
 constexpr int TC_EPI = 256;             // epilogue threads
-constexpr int TC_BUF = 32;              // buffered keys per epilogue thread
+constexpr int TC_BUF = 31;              // buffered keys per epilogue thread
 constexpr uint32_t TC_BOX = 128 * 128;  // bytes of one 128-row x 64-element BF16 box
 constexpr uint32_t TC_UNIT = 2 * TC_BOX;  // hi and lo boxes of one K slice
 constexpr uint64_t TC_WAIT = 2000000000ull;  // ns before a drain wait gives up (the default pipeline limit too)
@@ -63,9 +66,9 @@ struct TcCfg {
     static constexpr int STAGES = NBOX == 1 ? 4 : 3;  // ring of K slices
     static constexpr uint32_t A_BYTES = NBOX * TC_UNIT;
     static constexpr uint32_t BUF_BYTES = TC_BUF * TC_EPI * 8;
-    static constexpr int NBAR = 1 + 2 * STAGES + 6 + 1;  // a_full, b_full/empty, acc full/empty, yn_full, drain
+    static constexpr int NBAR = 1 + 2 * STAGES + 3 * TC_NACC + 1;  // a_full, b_full/empty, acc full/empty, yn_full, drain
     static constexpr uint32_t SMEM =
-        1024 + A_BYTES + STAGES * TC_UNIT + BUF_BYTES + 2 * TC_COLS * 4 + NBAR * 8 + 16;
+        1024 + A_BYTES + STAGES * TC_UNIT + BUF_BYTES + TC_NACC * TC_COLS * 4 + NBAR * 8 + 16;
     static_assert(SMEM <= 232448, "shared memory of one CTA");
 };
 
@@ -126,11 +129,11 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
     uint8_t *As = sm;                                   // NBOX x [hi box][lo box]
     uint8_t *Bs = As + Cfg::A_BYTES;                    // S stages of [hi box][lo box]
     uint64_t *sbuf = (uint64_t *)(Bs + S * TC_UNIT);    // [TC_BUF][TC_EPI] buffered (column, key bits)
-    float *s_yn = (float *)(sbuf + TC_BUF * TC_EPI);    // [2][TC_COLS] column norms
-    uint64_t *bars = (uint64_t *)(s_yn + 2 * TC_COLS);
+    float *s_yn = (float *)(sbuf + TC_BUF * TC_EPI);    // [TC_NACC][TC_COLS] column norms
+    uint64_t *bars = (uint64_t *)(s_yn + TC_NACC * TC_COLS);
     uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + S;
-    uint64_t *acc_full = bars + 1 + 2 * S, *acc_empty = bars + 3 + 2 * S, *yn_full = bars + 5 + 2 * S;
-    uint64_t *drain = bars + 7 + 2 * S;
+    uint64_t *acc_full = bars + 1 + 2 * S, *acc_empty = acc_full + TC_NACC, *yn_full = acc_empty + TC_NACC;
+    uint64_t *drain = yn_full + TC_NACC;
     uint32_t *tmem_slot = (uint32_t *)(bars + Cfg::NBAR);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -140,7 +143,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
             mbar_init(b_full + s, 1);
             mbar_init(b_empty + s, 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < TC_NACC; ++b) {
             mbar_init(acc_full + b, 1);
             mbar_init(acc_empty + b, TC_EPI / 32);
             mbar_init(yn_full + b, 1);
@@ -149,7 +152,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         fence_barrier_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, 2 * TC_COLS);
+        tmem_alloc(tmem_slot, TC_NACC * TC_COLS);
         tmem_relinquish();
     }
     fence_before_sync();
@@ -194,8 +197,8 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         bool ok = mbar_wait(a_full, 0, wait_ns);
         if (!ok) atomicOr(err, 2u);
         for (int t = 0; ok && t < ntiles; ++t) {
-            const int buf = t & 1;
-            if (t >= 2 && !mbar_wait(acc_empty + buf, ((t / 2) - 1) & 1, wait_ns)) {
+            const int buf = t % TC_NACC;
+            if (t >= TC_NACC && !mbar_wait(acc_empty + buf, ((t / TC_NACC) - 1) & 1, wait_ns)) {
                 atomicOr(err, 8u);
                 break;
             }
@@ -225,12 +228,12 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         mma_commit(drain);
         if (!mbar_wait(drain, 0, TC_WAIT)) atomicOr(err, 64u);
     } else if (warp == 2 && lane == 0) {
-        // ---- column norms of tile t into s_yn[t % 2], once the epilogue has
+        // ---- column norms of tile t into s_yn[t % TC_NACC], once the epilogue has
         // released that buffer (with the accumulator of tile t - 2)
         int issued = 0;
         for (int t = 0; t < ntiles; ++t) {
-            const int buf = t & 1;
-            if (t >= 2 && !mbar_wait(acc_empty + buf, ((t / 2) - 1) & 1, wait_ns)) {
+            const int buf = t % TC_NACC;
+            if (t >= TC_NACC && !mbar_wait(acc_empty + buf, ((t / TC_NACC) - 1) & 1, wait_ns)) {
                 atomicOr(err, 128u);
                 break;
             }
@@ -239,8 +242,8 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
             issued = t + 1;
         }
         bool landed = true;
-        for (int t = issued > 2 ? issued - 2 : 0; t < issued; ++t)
-            landed = mbar_wait(yn_full + (t & 1), (t / 2) & 1, TC_WAIT) && landed;
+        for (int t = issued > TC_NACC ? issued - TC_NACC : 0; t < issued; ++t)
+            landed = mbar_wait(yn_full + (t % TC_NACC), (t / TC_NACC) & 1, TC_WAIT) && landed;
         if (!landed) atomicOr(err, 256u);
     } else if (warp >= 4) {
         // ---- epilogue: thread r of warpgroup h owns row row0 + r (TMEM lane r)
@@ -274,11 +277,11 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         };
         bool ok = true;
         for (int t = 0; t < ntiles; ++t) {
-            const int buf = t & 1;
+            const int buf = t % TC_NACC;
             const int64_t c_base = (int64_t)t * TC_COLS;
             if (ok)
-                ok = __all_sync(FULL, mbar_wait(acc_full + buf, (t / 2) & 1, wait_ns) &&
-                                          mbar_wait(yn_full + buf, (t / 2) & 1, wait_ns));
+                ok = __all_sync(FULL, mbar_wait(acc_full + buf, (t / TC_NACC) & 1, wait_ns) &&
+                                          mbar_wait(yn_full + buf, (t / TC_NACC) & 1, wait_ns));
             if (!ok && lane == 0) atomicOr(err, 16u);
             fence_after_sync();
             if (ok) {
@@ -353,7 +356,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
     __syncthreads();
     if (warp == 1) {
         fence_after_sync();
-        tmem_dealloc(tmem, 2 * TC_COLS);
+        tmem_dealloc(tmem, TC_NACC * TC_COLS);
     }
 }
 

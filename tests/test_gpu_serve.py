@@ -27,9 +27,9 @@ D, K, N0 = 32, 10, 3000
 MIX = Mixture(d=D, components=12, half_width=10.0, sigma=1.0, seed=31)
 
 
-def make_graph(knn, capacity, max_batch=256):
-    cfg = knn.GraphConfig(dim=D, k=K, depth=2, speedup=4.0, expansion=5.0, max_batch=max_batch, seed=5,
-                          capacity=capacity)
+def make_graph(knn, capacity, max_batch=256, storage=0):
+    cfg = knn.GraphConfig(dim=D, k=K, depth=2, storage=storage, speedup=4.0, expansion=5.0,
+                          max_batch=max_batch, seed=5, capacity=capacity)
     return knn.Graph(cfg, cuda_tensor(MIX.sample(N0, 1)))
 
 
@@ -184,14 +184,16 @@ def test_capacity_refusal(knn):
         g.close()
 
 
-def test_reserve_keeps_the_graph(knn):
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_reserve_keeps_the_graph(knn, storage):
     """Growing a graph mid-stream (knn_graph_reserve) changes nothing the
-    method computes: the same inserts give the same lists as a graph created
-    with the larger capacity."""
+    method computes, for each searched copy (FP32, BF16, FP8 with its row
+    scales): the same inserts give the same lists as a graph created with
+    the larger capacity."""
     pts = MIX.sample(300, 41)
     lists = []
     for grow in (False, True):
-        g = make_graph(knn, N0 + (100 if grow else 300))
+        g = make_graph(knn, N0 + (100 if grow else 300), storage=storage)
         try:
             g.insert(cuda_tensor(pts[:100]))
             if grow:
