@@ -7,27 +7,27 @@
 // value in two BF16 parts, x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), and
 // accumulating hi.hi + hi.lo + lo.hi.
 //
-// One CTA owns 128 rows and streams every column (12 warps):
+// One CTA owns 128 rows and streams every column in 192-column tiles (16 warps):
 //   warp 0      TMA: the CTA's rows (hi and lo) once, then the column tiles,
 //               one 64-element K slice (hi and lo) per ring stage;
 //   warp 1      owns the TMEM allocation; one thread issues the MMAs of a
-//               128-column tile into one of four FP32 accumulators (all
-//               512 TMEM columns), so it can run three tiles ahead of the
-//               epilogue;
+//               192-column tile into one of two FP32 accumulators (256 TMEM
+//               columns apart, all 512 allocated), so it runs a tile ahead
+//               of the epilogue;
 //   warp 2      copies each tile's column norms beside its accumulator;
-//   warps 4..11 epilogue, two warpgroups: thread r of warpgroup h reads
+//   warps 4..15 epilogue, three warpgroups: thread r of warpgroup h reads
 //               accumulator lane r (its row), columns 64h .. 64h+63 of each
-//               tile, forms their keys and keeps the 32 smallest it sees.
-// A key below the thread's current 32nd is only appended to a per-thread
-// buffer in shared memory; when some lane's buffer is half full the warp
+//               tile, forms their keys and keeps the 24 smallest it sees.
+// A key below the thread's current 24th is only appended to a per-thread
+// buffer in shared memory; when some lane's buffer may not hold 16 more the warp
 // merges all buffers into the sorted lists in lockstep, so the costly
 // insertions of the 32 rows of a warp run together instead of one lane at
 // a time.
 //
-// The screening is then made exact.  The 64 candidates of a row (32 per
+// The screening is then made exact.  The 72 candidates of a row (24 per
 // warpgroup) are re-scored as FP32 squared differences and the k best kept.
-// Every other column has a screened key at least the smaller of the two
-// lists' 32nd keys; the row is accepted only if a proven bound on the
+// Every other column has a screened key at least the smallest of the three
+// lists' last keys; the row is accepted only if a proven bound on the
 // screening error shows that no such column can beat its k-th neighbour,
 // otherwise it is recomputed against every column in FP32 by the CUDA-core
 // kernel.  The lists therefore equal the exact ones up to FP32 rounding of
@@ -38,6 +38,7 @@
 // rows of that CTA are marked for the FP32 pass, so the result stays exact;
 // before the CTA exits, every copy and MMA it issued is waited for (drain
 // waits, on work that completes by itself) so that nothing is left in flight.
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -50,26 +51,35 @@ namespace knn {
 using namespace tc;
 
 constexpr int TC_ROWS = 128;            // rows per CTA (MMA M)
-constexpr int TC_COLS = 128;            // columns per tile (MMA N)
-constexpr int TC_NACC = 4;              // TMEM accumulators (all 512 columns): the MMAs run ahead by up to 3 tiles
-constexpr int TC_CAND = 32;             // candidates kept per row and warpgroup
-constexpr int TC_NCAND = 2 * TC_CAND;   // candidates per row
-constexpr int TC_EPI = 256;             // epilogue threads
-constexpr int TC_BUF = 31;              // buffered keys per epilogue thread
-constexpr uint32_t TC_BOX = 128 * 128;  // bytes of one 128-row x 64-element BF16 box
-constexpr uint32_t TC_UNIT = 2 * TC_BOX;  // hi and lo boxes of one K slice
+constexpr int TC_COLS = 192;            // columns per tile (MMA N)
+constexpr int TC_NWG = 3;               // epilogue warpgroups, each with its own columns of a tile
+constexpr int TC_WG_COLS = TC_COLS / TC_NWG;  // columns of a tile per epilogue thread
+constexpr int TC_ACC_STRIDE = TC_COLS <= 128 ? 128 : 256;  // TMEM columns from one accumulator to the next
+constexpr int TC_NACC = 512 / TC_ACC_STRIDE;  // TMEM accumulators: the MMAs run up to TC_NACC - 1 tiles ahead
+constexpr int TC_CAND = TC_NWG == 2 ? 32 : 24;  // candidates kept per row and warpgroup
+constexpr int TC_NCAND = TC_NWG * TC_CAND;  // candidates per row
+constexpr int TC_EPI = TC_NWG * 128;    // epilogue threads
+constexpr int TC_THREADS = 128 + TC_EPI;  // 4 warps for the copies, the MMAs and the norms, then the epilogue
+constexpr int TC_BUF = TC_NWG == 2 ? 31 : 20;  // buffered keys per epilogue thread
+constexpr uint32_t TC_BOX = 128 * 128;  // bytes of one 128-row x 64-element BF16 box (the CTA's rows)
+constexpr uint32_t TC_UNIT = 2 * TC_BOX;  // hi and lo boxes of one K slice of the rows
+constexpr uint32_t TC_BOX_B = TC_COLS * 128;  // the hi or the lo box of one K slice of a column tile
+constexpr uint32_t TC_STAGE = 2 * TC_BOX_B;     // a ring stage: both boxes of one K slice
+static_assert(TC_WG_COLS % 32 == 0, "an epilogue thread reads its columns 32 at a time");
+static_assert(TC_COLS % 16 == 0 && TC_COLS <= TC_ACC_STRIDE, "MMA N and accumulators in TMEM");
 constexpr uint64_t TC_WAIT = 2000000000ull;  // ns before a drain wait gives up (the default pipeline limit too)
 
-// NBOX 64-element K slices per row (padded width 64 * NBOX)
+// NBOX 64-element K slices per row (padded width 64 * NBOX); the ring takes
+// as many stages as the shared memory left holds
 template <int NBOX>
 struct TcCfg {
-    static constexpr int STAGES = NBOX == 1 ? 4 : 3;  // ring of K slices
     static constexpr uint32_t A_BYTES = NBOX * TC_UNIT;
     static constexpr uint32_t BUF_BYTES = TC_BUF * TC_EPI * 8;
+    static constexpr uint32_t FIXED = 1024 + A_BYTES + BUF_BYTES + TC_NACC * TC_COLS * 4 + (3 * TC_NACC + 2) * 8 + 16;
+    static constexpr int STAGES = (232448 - FIXED) / (TC_STAGE + 16) < 8 ? (232448 - FIXED) / (TC_STAGE + 16) : 8;
     static constexpr int NBAR = 1 + 2 * STAGES + 3 * TC_NACC + 1;  // a_full, b_full/empty, acc full/empty, yn_full, drain
-    static constexpr uint32_t SMEM =
-        1024 + A_BYTES + STAGES * TC_UNIT + BUF_BYTES + TC_NACC * TC_COLS * 4 + NBAR * 8 + 16;
-    static_assert(SMEM <= 232448, "shared memory of one CTA");
+    static constexpr uint32_t SMEM = FIXED + STAGES * (TC_STAGE + 16);
+    static_assert(STAGES >= 2 && SMEM <= 232448, "shared memory of one CTA");
 };
 
 // x -> (hi, lo) BF16 rows of width dpt (zero padded) and FP32 squared norms;
@@ -117,18 +127,20 @@ __device__ __forceinline__ void cand_insert(float (&key)[TC_CAND], int (&id)[TC_
 }
 
 template <int NBOX>
-__global__ void __launch_bounds__(384, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
 exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant__ CUtensorMap t_lo,
-                const float *__restrict__ norm2, int64_t n, int32_t *cand_id, float *cand_key,
-                unsigned *err, uint64_t wait_ns) {
+                const __grid_constant__ CUtensorMap t_bhi, const __grid_constant__ CUtensorMap t_blo,
+                const float *__restrict__ norm2, int64_t n, int64_t full_blocks, int parts,
+                int32_t *cand_id, float *cand_key, int32_t *part_id, float *part_key, unsigned *err,
+                uint64_t wait_ns) {
     using Cfg = TcCfg<NBOX>;
     constexpr int S = Cfg::STAGES;
     extern __shared__ uint8_t tc_raw[];
     // 128-byte swizzled tiles want 1024-byte aligned shared memory
     uint8_t *sm = (uint8_t *)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *As = sm;                                   // NBOX x [hi box][lo box]
-    uint8_t *Bs = As + Cfg::A_BYTES;                    // S stages of [hi box][lo box]
-    uint64_t *sbuf = (uint64_t *)(Bs + S * TC_UNIT);    // [TC_BUF][TC_EPI] buffered (column, key bits)
+    uint8_t *Bs = As + Cfg::A_BYTES;                    // S ring stages
+    uint64_t *sbuf = (uint64_t *)(Bs + S * TC_STAGE);   // [TC_BUF][TC_EPI] buffered (column, key bits)
     float *s_yn = (float *)(sbuf + TC_BUF * TC_EPI);    // [TC_NACC][TC_COLS] column norms
     uint64_t *bars = (uint64_t *)(s_yn + TC_NACC * TC_COLS);
     uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + S;
@@ -152,25 +164,39 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         fence_barrier_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, TC_NACC * TC_COLS);
+        tmem_alloc(tmem_slot, TC_NACC * TC_ACC_STRIDE);
         tmem_relinquish();
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const int64_t row0 = (int64_t)blockIdx.x * TC_ROWS;
-    const int ntiles = (int)((n + TC_COLS - 1) / TC_COLS);
+    // CTAs below full_blocks take every column tile of their row block; the
+    // rest split the row blocks after those into `parts` runs of tiles each
+    const int all_tiles = (int)((n + TC_COLS - 1) / TC_COLS);
+    int64_t rb = blockIdx.x;
+    int part = -1, t0 = 0, ntiles = all_tiles;
+    if (rb >= full_blocks) {
+        const int64_t j = rb - full_blocks;
+        rb = full_blocks + j / parts;
+        part = (int)(j % parts);
+        t0 = (int)((int64_t)all_tiles * part / parts);
+        ntiles = (int)((int64_t)all_tiles * (part + 1) / parts) - t0;
+    }
+    const int64_t row0 = rb * TC_ROWS;
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer
         prefetch_tensormap(&t_hi);
         prefetch_tensormap(&t_lo);
+        prefetch_tensormap(&t_bhi);
+        prefetch_tensormap(&t_blo);
         mbar_arrive_expect_tx(a_full, Cfg::A_BYTES);
         for (int kb = 0; kb < NBOX; ++kb) {
             tma_load_2d(As + kb * TC_UNIT, &t_hi, a_full, kb * 64, (int)row0);
             tma_load_2d(As + kb * TC_UNIT + TC_BOX, &t_lo, a_full, kb * 64, (int)row0);
         }
+        // unit u: K slice u % NBOX of column tile u / NBOX
         const int units = ntiles * NBOX;
         int issued = 0;
         for (int u = 0; u < units; ++u) {
@@ -179,11 +205,10 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                 atomicOr(err, 1u);
                 break;
             }
-            const int t = u / NBOX, kb = u % NBOX;
-            uint8_t *B = Bs + s * TC_UNIT;
-            mbar_arrive_expect_tx(b_full + s, TC_UNIT);
-            tma_load_2d(B, &t_hi, b_full + s, kb * 64, t * TC_COLS);
-            tma_load_2d(B + TC_BOX, &t_lo, b_full + s, kb * 64, t * TC_COLS);
+            const int t = t0 + u / NBOX, kb = u % NBOX;
+            mbar_arrive_expect_tx(b_full + s, TC_STAGE);
+            tma_load_2d(Bs + s * TC_STAGE, &t_bhi, b_full + s, kb * 64, t * TC_COLS);
+            tma_load_2d(Bs + s * TC_STAGE + TC_BOX_B, &t_blo, b_full + s, kb * 64, t * TC_COLS);
             issued = u + 1;
         }
         // no copy may still be in flight when the CTA exits
@@ -202,7 +227,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                 atomicOr(err, 8u);
                 break;
             }
-            const uint32_t d = tmem + buf * TC_COLS;
+            const uint32_t d = tmem + buf * TC_ACC_STRIDE;
             for (int kb = 0; kb < NBOX; ++kb) {
                 const int u = t * NBOX + kb, s = u % S;
                 if (!mbar_wait(b_full + s, (u / S) & 1, wait_ns)) {
@@ -213,8 +238,8 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                 fence_after_sync();
                 const uint64_t ah = sdesc_k_sw128(smem_u32(As + kb * TC_UNIT));
                 const uint64_t al = sdesc_k_sw128(smem_u32(As + kb * TC_UNIT + TC_BOX));
-                const uint64_t bh = sdesc_k_sw128(smem_u32(Bs + s * TC_UNIT));
-                const uint64_t bl = sdesc_k_sw128(smem_u32(Bs + s * TC_UNIT + TC_BOX));
+                const uint64_t bh = sdesc_k_sw128(smem_u32(Bs + s * TC_STAGE));
+                const uint64_t bl = sdesc_k_sw128(smem_u32(Bs + s * TC_STAGE + TC_BOX_B));
                 for (int kk = 0; kk < 4; ++kk) {  // K step of 16 BF16 = 32 bytes = 2 descriptor units
                     mma_bf16(d, ah + 2 * kk, bh + 2 * kk, idesc, (kb | kk) != 0);
                     mma_bf16(d, ah + 2 * kk, bl + 2 * kk, idesc, 1u);
@@ -238,7 +263,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                 break;
             }
             mbar_arrive_expect_tx(yn_full + buf, TC_COLS * 4);
-            bulk_load(s_yn + buf * TC_COLS, norm2 + (int64_t)t * TC_COLS, TC_COLS * 4, yn_full + buf);
+            bulk_load(s_yn + buf * TC_COLS, norm2 + (int64_t)(t0 + t) * TC_COLS, TC_COLS * 4, yn_full + buf);
             issued = t + 1;
         }
         bool landed = true;
@@ -259,7 +284,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
             key[i] = __int_as_float(0x7f800000);
             id[i] = -1;
         }
-        float thr = __int_as_float(0x7f800000);  // current 32nd key
+        float thr = __int_as_float(0x7f800000);  // current TC_CAND-th key
         int cnt = 0;                              // buffered entries
         auto flush = [&]() {
             const int m = __reduce_max_sync(FULL, cnt);
@@ -278,16 +303,16 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         bool ok = true;
         for (int t = 0; t < ntiles; ++t) {
             const int buf = t % TC_NACC;
-            const int64_t c_base = (int64_t)t * TC_COLS;
+            const int64_t c_base = (int64_t)(t0 + t) * TC_COLS;
             if (ok)
                 ok = __all_sync(FULL, mbar_wait(acc_full + buf, (t / TC_NACC) & 1, wait_ns) &&
                                           mbar_wait(yn_full + buf, (t / TC_NACC) & 1, wait_ns));
             if (!ok && lane == 0) atomicOr(err, 16u);
             fence_after_sync();
             if (ok) {
-                const uint32_t ta = tmem + lane_base + buf * TC_COLS + 64 * h;
-                const float *yn = s_yn + buf * TC_COLS + 64 * h;
-                const uint32_t col0 = (uint32_t)c_base + 64 * h;
+                const uint32_t ta = tmem + lane_base + buf * TC_ACC_STRIDE + TC_WG_COLS * h;
+                const float *yn = s_yn + buf * TC_COLS + TC_WG_COLS * h;
+                const uint32_t col0 = (uint32_t)c_base + TC_WG_COLS * h;
                 // 16 columns: keys, then per group of 4 their minimum; only
                 // the groups where some lane of the warp has a key below its
                 // threshold run the appends, so that the common case takes no
@@ -329,7 +354,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                     }
                 };
 #pragma unroll 1
-                for (int c = 0; c < 64; c += 32) {
+                for (int c = 0; c < TC_WG_COLS; c += 32) {
                     uint32_t v[32];
                     tmem_ld32_async(ta + c, v);
                     tmem_wait_ld(v);
@@ -343,12 +368,15 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         }
         flush();
         if (row < n) {
-            int32_t *ci = cand_id + row * TC_NCAND + h * TC_CAND;
-            float *ck = cand_key + row * TC_NCAND + h * TC_CAND;
+            // a part's lists go to the part area, to be merged per row
+            const int64_t at = part < 0 ? row * TC_NCAND
+                                        : ((row - full_blocks * TC_ROWS) * parts + part) * TC_NCAND;
+            int32_t *ci = (part < 0 ? cand_id : part_id) + at + h * TC_CAND;
+            float *ck = (part < 0 ? cand_key : part_key) + at + h * TC_CAND;
 #pragma unroll
             for (int i = 0; i < TC_CAND; ++i) {
                 ci[i] = ok ? id[i] : -1;  // no candidates: the FP32 pass takes the row
-                ck[i] = key[i];
+                ck[i] = ok ? key[i] : -__int_as_float(0x7f800000);
             }
         }
     }
@@ -356,7 +384,68 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
     __syncthreads();
     if (warp == 1) {
         fence_after_sync();
-        tmem_dealloc(tmem, TC_NACC * TC_COLS);
+        tmem_dealloc(tmem, TC_NACC * TC_ACC_STRIDE);
+    }
+}
+
+// The row blocks split into parts: one warp per (row, warpgroup list) merges
+// the parts' sorted lists into the TC_CAND smallest keys, written where an
+// unsplit row keeps its list.  Parts cover disjoint columns; a column left
+// out has a key at least the merged last key (it lost the merge) or its own
+// part's last key, which is at least the merged last key.  A part that gave
+// up (ids -1, first key -inf) empties the row's list, so the FP32 pass takes
+// the row.
+__global__ void tc_merge_parts_kernel(int64_t n, int64_t row_begin, int parts, const int32_t *part_id,
+                                      const float *part_key, int32_t *cand_id, float *cand_key) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t row = row_begin + w / TC_NWG;
+    const int h = (int)(w % TC_NWG);
+    if (row >= n) return;  // warp-uniform
+    const float INF = __int_as_float(0x7f800000);
+    const int64_t base = (row - row_begin) * parts;
+    const int32_t *pid = part_id + (base + lane) * TC_NCAND + h * TC_CAND;
+    const float *pkey = part_key + (base + lane) * TC_NCAND + h * TC_CAND;
+    int pos = 0;
+    int32_t hid = -1;
+    float hkey = INF;
+    bool failed = false;
+    if (lane < parts) {
+        hid = pid[0];
+        hkey = pkey[0];
+        failed = hid < 0 && hkey == -INF;
+        if (hid < 0) hkey = INF;
+    }
+    failed = __any_sync(FULL, failed);
+    int32_t my_id = -1;
+    float my_key = INF;
+#pragma unroll 1
+    for (int i = 0; i < TC_CAND; ++i) {
+        float m = hkey;
+        int who = lane;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const float om = __shfl_xor_sync(FULL, m, off);
+            const int ow = __shfl_xor_sync(FULL, who, off);
+            if (om < m || (om == m && ow < who)) {
+                m = om;
+                who = ow;
+            }
+        }
+        const int32_t wid = __shfl_sync(FULL, hid, who);
+        if (lane == i) {
+            my_id = m < INF ? wid : -1;
+            my_key = m;
+        }
+        if (lane == who && m < INF) {
+            ++pos;
+            hid = pos < TC_CAND ? pid[pos] : -1;
+            hkey = hid >= 0 ? pkey[pos] : INF;
+        }
+    }
+    if (lane < TC_CAND) {
+        cand_id[row * TC_NCAND + h * TC_CAND + lane] = failed ? -1 : my_id;
+        cand_key[row * TC_NCAND + h * TC_CAND + lane] = my_key;
     }
 }
 
@@ -377,7 +466,7 @@ __device__ __forceinline__ float screening_error(float xnorm, float xn, float ym
     return 2.0f * (2.0f * dot + rest);
 }
 
-// One warp per row: FP32 re-score of the 64 candidates, the k best written
+// One warp per row: FP32 re-score of the 72 candidates, the k best written
 // as the row's list, and the exactness test of the screening.  Rows that
 // fail are appended to `redo`.
 template <int DP>
@@ -396,8 +485,8 @@ __global__ void tc_rescore_kernel(const float *X, const float *norm2, const unsi
     int full = 0;  // warpgroup lists holding TC_CAND candidates
     float thr = __int_as_float(0x7f800000);
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        const int32_t cid = cand_id[u * TC_NCAND + h * TC_CAND + lane];
+    for (int h = 0; h < TC_NWG; ++h) {
+        const int32_t cid = lane < TC_CAND ? cand_id[u * TC_NCAND + h * TC_CAND + lane] : -1;
         const int nc = __popc(__ballot_sync(FULL, cid >= 0));  // candidates fill a prefix
         const float d2 = gather_d2<ST_FP32, DP>(src, cid >= 0 ? (uint32_t)cid : 0u, nc, qv);
         for (int i = 0; i < nc; ++i)
@@ -414,7 +503,7 @@ __global__ void tc_rescore_kernel(const float *X, const float *norm2, const unsi
     // true squared distance >= thr + ||x||^2 - E.  The k-th re-scored
     // distance (FP32, relative error below (DP + 2) 2^-24) must lie below.
     bool exact = false;
-    if (full == 2) {
+    if (full == TC_NWG) {
         const float dk = key_d2(top.entry(k - 1));
         const float xn = norm2[u];
         const float E = screening_error(sqrtf(xn), xn, __uint_as_float(*norm_max), dpt);
@@ -439,14 +528,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// rows x dpt BF16 matrix, boxes of 128 rows x 64 elements, 128-byte swizzle;
-// rows past the end read as zeros
-static bool bf16_rows_map(CUtensorMap *m, const void *ptr, int64_t rows, int dpt) {
+// rows x dpt BF16 matrix, boxes of box_rows rows x 64 elements, 128-byte
+// swizzle; rows past the end read as zeros
+static bool bf16_rows_map(CUtensorMap *m, const void *ptr, int64_t rows, int dpt, int box_rows) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)dpt, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)dpt * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)TC_ROWS};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -458,17 +547,43 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 bool exact_tc_supported(int dp, int64_t n, int k, const uint32_t *removed) {
     return removed == nullptr && dp <= 128 && n >= TC_ROWS && n < (int64_t)INT32_MAX && k >= 1 &&
-           k <= TC_CAND && tensor_map_encoder() != nullptr;
+           k <= 32 && tensor_map_encoder() != nullptr;
+}
+
+// One CTA fits on an SM, so the row blocks run in waves of `sms` CTAs.  The
+// row blocks of a last, partly filled wave are split into runs of column
+// tiles, `parts` CTAs each, so that this wave ends about when a whole-row
+// CTA would have done 1 / parts of its work.
+constexpr int TC_SPLIT_MAX = 8;     // parts of one row block at most
+constexpr int TC_SPLIT_CTAS = 256;  // CTAs of the split wave at most
+struct TcPlan {
+    int64_t full_blocks;  // row blocks taken whole, by CTAs 0 .. full_blocks-1
+    int parts;            // CTAs per row block after those
+    int64_t grid;
+};
+static TcPlan tc_plan(int64_t n, int sms) {
+    const int64_t blocks = (n + TC_ROWS - 1) / TC_ROWS, tiles = (n + TC_COLS - 1) / TC_COLS;
+    const int64_t rem = sms > 0 ? blocks % sms : 0;
+    const int64_t parts =
+        rem ? std::min(std::min<int64_t>(sms / rem, tiles), std::min<int64_t>(TC_SPLIT_MAX, TC_SPLIT_CTAS / rem)) : 1;
+    if (parts < 2) return {blocks, 1, blocks};
+    return {blocks - rem, (int)parts, blocks - rem + rem * parts};
+}
+// rows x parts of the split wave's lists, at most
+static size_t tc_part_slots(int64_t n) {
+    const int64_t blocks = (n + TC_ROWS - 1) / TC_ROWS;
+    return (size_t)std::min<int64_t>(TC_SPLIT_CTAS, blocks * TC_SPLIT_MAX) * TC_ROWS;
 }
 
 // scratch, each part 256-byte aligned: hi, lo, norm2, cand_id, cand_key,
 // redo, counters[16] = {norm max, redo count, wait error, ...}, partial
-// lists of the FP32 pass
+// lists of the FP32 pass, the split wave's part_id and part_key
 size_t exact_tc_scratch_bytes(int64_t n, int dp) {
     const size_t dpt = tc_width(dp);
     const size_t n_pad = (size_t)(n + TC_COLS - 1) / TC_COLS * TC_COLS;
     return 2 * align256((size_t)n * dpt * 2) + align256(n_pad * 4) + 2 * align256((size_t)n * TC_NCAND * 4) +
-           align256((size_t)n * 4) + 256 + align256((size_t)EXACT_PARTIAL_SLOTS * 32 * 8);
+           align256((size_t)n * 4) + 256 + align256((size_t)EXACT_PARTIAL_SLOTS * 32 * 8) +
+           2 * align256(tc_part_slots(n) * TC_NCAND * 4);
 }
 
 static uint64_t g_tc_wait_ns = TC_WAIT;
@@ -476,14 +591,20 @@ static uint64_t g_tc_wait_ns = TC_WAIT;
 void exact_tc_set_wait(int64_t ns) { g_tc_wait_ns = ns < 0 ? TC_WAIT : (uint64_t)ns; }
 
 template <int NBOX>
-static cudaError_t tc_screen(const CUtensorMap &th, const CUtensorMap &tl, const float *norm2, int64_t n,
-                             int32_t *cid, float *ckey, unsigned *err, cudaStream_t s) {
+static cudaError_t tc_screen(const CUtensorMap &th, const CUtensorMap &tl, const CUtensorMap &tbh,
+                             const CUtensorMap &tbl, const float *norm2, int64_t n, const TcPlan &plan,
+                             int32_t *cid, float *ckey, int32_t *pid, float *pkey, unsigned *err, cudaStream_t s) {
     const size_t smem = TcCfg<NBOX>::SMEM;
     cudaError_t e =
         cudaFuncSetAttribute(exact_tc_kernel<NBOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    exact_tc_kernel<NBOX><<<(unsigned)((n + TC_ROWS - 1) / TC_ROWS), 384, smem, s>>>(th, tl, norm2, n, cid, ckey,
-                                                                                     err, g_tc_wait_ns);
+    exact_tc_kernel<NBOX><<<(unsigned)plan.grid, TC_THREADS, smem, s>>>(
+        th, tl, tbh, tbl, norm2, n, plan.full_blocks, plan.parts, cid, ckey, pid, pkey, err, g_tc_wait_ns);
+    if ((e = cudaGetLastError()) != cudaSuccess || plan.parts < 2) return e;
+    const int64_t row_begin = plan.full_blocks * TC_ROWS;
+    const int64_t threads = (n - row_begin) * TC_NWG * 32;
+    tc_merge_parts_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, row_begin, plan.parts, pid, pkey,
+                                                                             cid, ckey);
     return cudaGetLastError();
 }
 
@@ -513,15 +634,25 @@ cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned 
     auto *redo = (int32_t *)take((size_t)a.n * 4);
     auto *counters = (unsigned *)take(64);
     auto *partial = (uint64_t *)take((size_t)EXACT_PARTIAL_SLOTS * 32 * 8);
+    auto *pid = (int32_t *)take(tc_part_slots(a.n) * TC_NCAND * 4);
+    auto *pkey = (float *)take(tc_part_slots(a.n) * TC_NCAND * 4);
     *counters_out = counters;
-    CUtensorMap th, tl;
-    if (!bf16_rows_map(&th, hi, a.n, dpt) || !bf16_rows_map(&tl, lo, a.n, dpt)) return cudaErrorNotSupported;
-    cudaError_t e = cudaMemsetAsync(counters, 0, 64, s);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const TcPlan plan = tc_plan(a.n, sms);
+    // the CTA's rows in 128-row boxes, the column tiles in TC_COLS-row boxes
+    CUtensorMap th, tl, tbh, tbl;
+    if (!bf16_rows_map(&th, hi, a.n, dpt, TC_ROWS) || !bf16_rows_map(&tl, lo, a.n, dpt, TC_ROWS) ||
+        !bf16_rows_map(&tbh, hi, a.n, dpt, TC_COLS) || !bf16_rows_map(&tbl, lo, a.n, dpt, TC_COLS))
+        return cudaErrorNotSupported;
+    e = cudaMemsetAsync(counters, 0, 64, s);
     if (e != cudaSuccess) return e;
     tc_split_kernel<<<(unsigned)((n_pad * 32 + 255) / 256), 256, 0, s>>>(a.X, a.n, n_pad, dp, dpt, hi, lo,
                                                                           norm2, counters);
-    e = dpt == 64 ? tc_screen<1>(th, tl, norm2, a.n, cid, ckey, counters + 2, s)
-                  : tc_screen<2>(th, tl, norm2, a.n, cid, ckey, counters + 2, s);
+    e = dpt == 64 ? tc_screen<1>(th, tl, tbh, tbl, norm2, a.n, plan, cid, ckey, pid, pkey, counters + 2, s)
+                  : tc_screen<2>(th, tl, tbh, tbl, norm2, a.n, plan, cid, ckey, pid, pkey, counters + 2, s);
     if (e != cudaSuccess) return e;
     switch (dp) {
         case 16: e = tc_rescore<16>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
@@ -538,9 +669,6 @@ cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned 
     e = cudaMemcpyAsync(&nredo, counters + 1, sizeof nredo, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess || nredo == 0) return e;
-    int dev = 0, sms = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     ExactArgs rest = a;
     rest.rows = redo;
     rest.row_count = counters + 1;

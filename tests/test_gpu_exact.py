@@ -118,8 +118,22 @@ def test_exact_tensor_cores_refuse_what_they_cannot_do(knn):
         knn.knn_exact_set_path("auto")
 
 
+@pytest.mark.parametrize("n,d,k,seed", [(20_000, 128, 10, 13), (9_000, 16, 20, 14)])
+def test_exact_tensor_cores_split_last_wave(knn, n, d, k, seed):
+    """The row blocks of the last, partly filled wave of CTAs are screened in
+    column parts and their lists merged per row: every one of the last 1,024
+    rows (where those blocks lie) and 64 others against the oracle."""
+    X = Mixture(d=d, components=30, half_width=10.0, sigma=1.0, seed=seed).sample(n, 4)
+    ids, sims = gpu_exact(knn, X, k, "tensor_cores")
+    assert knn.knn_exact_last_info()["rows_redone"] <= n // 100
+    rng = np.random.default_rng(seed)
+    rows = np.concatenate([rng.choice(n - 1024, 64, replace=False), np.arange(n - 1024, n)])
+    o_ids, o_sims, margin = oracle.exact_knn(X, k, rows=rows)
+    check_rows(ids[rows], sims[rows], o_ids, o_sims, margin, exact_tol(d))
+
+
 def test_exact_graph_full_size_sampled_rows(knn):
-    """The 100,000-point, d = 128 initial graph: 48 sampled rows against the
+    """The 100,000-point, d = 128 initial graph: 64 sampled rows against the
     oracle, and the list invariants on every row."""
     X = PLAIN_D128.initial()
     k = PLAIN_D128.k
@@ -127,7 +141,11 @@ def test_exact_graph_full_size_sampled_rows(knn):
     info = knn.knn_exact_last_info()
     assert info["path"] == "tensor_cores"
     assert info["rows_redone"] <= X.shape[0] // 100   # the screening settles almost every row
-    rows = np.random.default_rng(5).choice(X.shape[0], 48, replace=False)
+    # 48 rows anywhere and 16 of the last 2,048, where the last wave's row
+    # blocks are screened in column parts
+    rng = np.random.default_rng(5)
+    rows = np.concatenate([rng.choice(X.shape[0] - 2048, 48, replace=False),
+                           X.shape[0] - 2048 + rng.choice(2048, 16, replace=False)])
     o_ids, o_sims, margin = oracle.exact_knn(X, k, rows=rows)
     check_rows(ids[rows], sims[rows], o_ids, o_sims, margin, exact_tol(128))
     n = X.shape[0]
