@@ -274,7 +274,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         // ---- epilogue: thread r of warpgroup h owns row row0 + r (TMEM lane r)
         const int te = threadIdx.x - 128;
         const int h = te >> 7, r = te & 127;
-        const int64_t row = row0 + r;
+        const uint32_t row = (uint32_t)(row0 + r);  // rows and columns are below 2^31
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         uint64_t *mybuf = sbuf + te;  // entry e at mybuf[e * TC_EPI]
         float key[TC_CAND];
@@ -293,17 +293,16 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                 if (e < cnt) {
                     const uint2 ent = reinterpret_cast<const uint2 *>(mybuf)[e * TC_EPI];
                     const float kk = __uint_as_float(ent.y);
-                    const int col = (int)ent.x;
-                    if (kk < key[TC_CAND - 1] && (int64_t)col != row) cand_insert(key, id, kk, col);
+                    if (kk < key[TC_CAND - 1] && ent.x != row) cand_insert(key, id, kk, (int)ent.x);
                 }
             }
             cnt = 0;
             thr = key[TC_CAND - 1];
         };
         bool ok = true;
-        for (int t = 0; t < ntiles; ++t) {
+        uint32_t c_base = (uint32_t)t0 * TC_COLS;  // first column of tile t0 + t
+        for (int t = 0; t < ntiles; ++t, c_base += TC_COLS) {
             const int buf = t % TC_NACC;
-            const int64_t c_base = (int64_t)(t0 + t) * TC_COLS;
             if (ok)
                 ok = __all_sync(FULL, mbar_wait(acc_full + buf, (t / TC_NACC) & 1, wait_ns) &&
                                           mbar_wait(yn_full + buf, (t / TC_NACC) & 1, wait_ns));
@@ -367,12 +366,19 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
             if (lane == 0) mbar_arrive(acc_empty + buf);
         }
         flush();
-        if (row < n) {
+        // (the block's place is recomputed here rather than kept in registers
+        // through the scan)
+        const int64_t orow = (int64_t)blockIdx.x < full_blocks
+                                 ? (int64_t)blockIdx.x * TC_ROWS + r
+                                 : (full_blocks + ((int64_t)blockIdx.x - full_blocks) / parts) * TC_ROWS + r;
+        if (orow < n) {
             // a part's lists go to the part area, to be merged per row
-            const int64_t at = part < 0 ? row * TC_NCAND
-                                        : ((row - full_blocks * TC_ROWS) * parts + part) * TC_NCAND;
-            int32_t *ci = (part < 0 ? cand_id : part_id) + at + h * TC_CAND;
-            float *ck = (part < 0 ? cand_key : part_key) + at + h * TC_CAND;
+            const bool split = (int64_t)blockIdx.x >= full_blocks;
+            const int64_t at = !split ? orow * TC_NCAND
+                                      : ((orow - full_blocks * TC_ROWS) * parts +
+                                         ((int64_t)blockIdx.x - full_blocks) % parts) * TC_NCAND;
+            int32_t *ci = (split ? part_id : cand_id) + at + h * TC_CAND;
+            float *ck = (split ? part_key : cand_key) + at + h * TC_CAND;
 #pragma unroll
             for (int i = 0; i < TC_CAND; ++i) {
                 ci[i] = ok ? id[i] : -1;  // no candidates: the FP32 pass takes the row
