@@ -318,19 +318,29 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                 // divergent branch
                 auto scan16 = [&](const uint32_t(&v)[16], int c) {
                     float kv[16];
+                    const unsigned long long m2 = f32x2_pack(-2.0f, -2.0f);
 #pragma unroll
                     for (int j4 = 0; j4 < 4; ++j4) {
                         const float4 y = *reinterpret_cast<const float4 *>(yn + c + 4 * j4);
-                        kv[4 * j4 + 0] = fmaf(-2.0f, __uint_as_float(v[4 * j4 + 0]), y.x);
-                        kv[4 * j4 + 1] = fmaf(-2.0f, __uint_as_float(v[4 * j4 + 1]), y.y);
-                        kv[4 * j4 + 2] = fmaf(-2.0f, __uint_as_float(v[4 * j4 + 2]), y.z);
-                        kv[4 * j4 + 3] = fmaf(-2.0f, __uint_as_float(v[4 * j4 + 3]), y.w);
+                        // two keys an instruction, each rounded as fmaf would
+                        unsigned long long k01, k23;
+                        asm("fma.rn.f32x2 %0, %1, %2, %3;"
+                            : "=l"(k01)
+                            : "l"(f32x2_pack(__uint_as_float(v[4 * j4]), __uint_as_float(v[4 * j4 + 1]))), "l"(m2),
+                              "l"(f32x2_pack(y.x, y.y)));
+                        asm("fma.rn.f32x2 %0, %1, %2, %3;"
+                            : "=l"(k23)
+                            : "l"(f32x2_pack(__uint_as_float(v[4 * j4 + 2]), __uint_as_float(v[4 * j4 + 3]))),
+                              "l"(m2), "l"(f32x2_pack(y.z, y.w)));
+                        asm("mov.b64 {%0, %1}, %2;" : "=f"(kv[4 * j4]), "=f"(kv[4 * j4 + 1]) : "l"(k01));
+                        asm("mov.b64 {%0, %1}, %2;" : "=f"(kv[4 * j4 + 2]), "=f"(kv[4 * j4 + 3]) : "l"(k23));
                     }
                     unsigned g = 0;
 #pragma unroll
                     for (int j4 = 0; j4 < 4; ++j4) {
-                        const float mn =
-                            fminf(fminf(kv[4 * j4], kv[4 * j4 + 1]), fminf(kv[4 * j4 + 2], kv[4 * j4 + 3]));
+                        float m3, mn;
+                        asm("min.f32 %0, %1, %2, %3;" : "=f"(m3) : "f"(kv[4 * j4]), "f"(kv[4 * j4 + 1]), "f"(kv[4 * j4 + 2]));
+                        mn = fminf(m3, kv[4 * j4 + 3]);
                         g |= (unsigned)(mn < thr) << j4;
                     }
                     g = __reduce_or_sync(FULL, g);
