@@ -218,6 +218,54 @@ KNN_API knn_status knn_graph_query_partitioned_ids(knn_graph *g, const float *ve
                                                    void *stream);
 
 /*
+ * Distributed online build (Sec. 7, Algorithm 5) on one device.  The graph's
+ * n nodes are split in `parts` partitions by labels [n] (int32, 0..parts-1,
+ * host or device), each with a medoid (medoids [parts], node ids, host or
+ * device): for instance knn_balanced_kmedoids' clusters, in any node order.
+ * The state lives on the device with the graph, sized for its capacity.
+ * recompute_interval >= 0: the medoids are recomputed (Algorithm 4's update
+ * step: in every non-empty partition the member with the smallest sum of
+ * Euclidean distances to the other members, ties to the lower id) after each
+ * insert batch that leaves the graph at least recompute_interval * n_last
+ * nodes larger than it was at the last recompute (n_last: its size at this
+ * call, then at each recompute); 0 never recomputes.  Returns
+ * KNN_ERR_INVALID_ARG for labels or medoids out of range,
+ * KNN_ERR_UNSUPPORTED for parts outside 1..min(KNN_MAX_PARTS, max_batch) or a
+ * graph with removed nodes, KNN_ERR_OOM when the state does not fit.
+ * Synchronises `stream`.
+ */
+KNN_API knn_status knn_graph_set_partitions(knn_graph *g, const int32_t *labels, const int64_t *medoids,
+                                            int32_t parts, double recompute_interval, void *stream);
+
+/*
+ * Algorithm 5 for a batch of m new points (as knn_graph_insert_batch, whose
+ * arguments, outputs and errors it shares): the search of every new point is
+ * the distributed search (Algorithm 3) over the partitions -- partition j is
+ * searched on its own subgraph (its nodes in id order, the entries of their
+ * lists inside it; restart draws among its nodes, budget
+ * max(1, floor(size / speedup)), restart stream new id + j * 2^56), and the k
+ * most similar of all the partitions' candidates are kept, ties to the lower
+ * id.  The batch then joins the graph as in knn_graph_insert_batch (its own
+ * similarities and Update, Algorithm 2, over the whole graph), every new node
+ * is given to the partition of its most similar medoid (ties to the lower
+ * partition), and the medoids are recomputed when recompute_interval says
+ * so.  With one partition this is knn_graph_insert_batch.  Requires
+ * knn_graph_set_partitions; KNN_ERR_UNSUPPORTED once nodes were removed.
+ * Synchronises `stream` (the partition sizes are read on the host).
+ */
+KNN_API knn_status knn_graph_insert_distributed(knn_graph *g, const float *vecs, int64_t m, int64_t *out_ids,
+                                                int64_t *out_nbrs, void *stream);
+
+/*
+ * The partition state: labels [n] (int32), medoids [parts] (node ids) and
+ * the number of medoid recomputes so far, each nullable, host or device
+ * buffers.  KNN_ERR_INVALID_ARG without knn_graph_set_partitions.
+ * Synchronises `stream`.
+ */
+KNN_API knn_status knn_graph_get_partitions(knn_graph *g, int32_t *labels, int64_t *medoids, int64_t *recomputes,
+                                            void *stream);
+
+/*
  * Remove m nodes (not in the paper).  Removed nodes are never drawn, climbed
  * to, returned or offered again; lists that still hold them keep the entry.
  * KNN_ERR_NOT_FOUND if an id is outside 0 .. n-1.  ids: [m] int64.

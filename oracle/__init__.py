@@ -15,6 +15,12 @@ Every function cites the passage of the paper it follows:
 * :func:`rescore`       exact re-score of screening candidates.
 * :func:`update`        Update (Algorithm 2).
 * :func:`insert_stream` sequential online build (Algorithm 1).
+* :func:`partitioned_search`, :func:`partitioned_search_labels`  distributed
+  search (Sec. 6, Algorithm 3).
+* :func:`kmedoids` and its steps  balanced k-medoids (Sec. 7, Algorithm 4).
+* :func:`nearest_medoid`, :func:`medoid_recompute_sizes`,
+  :func:`distributed_insert_stream`  distributed online build (Sec. 7,
+  Algorithm 5; the recompute interval of Sec. 8).
 * :func:`correct_edges`, :func:`quality_q`  graph quality (Sec. 8.5).
 * :func:`quantize_bf16`, :func:`quantize_e4m3`  screening storage codes.
 """
@@ -315,6 +321,133 @@ def partitioned_search(X, nbr_ids, q, k_out: int, part_offsets, speedup: float, 
     kk = min(k_out, len(ids))
     out_ids[:kk], out_sims[:kk] = ids[:kk], sims[:kk]
     return out_ids, out_sims, tot, margin
+
+
+def partitioned_search_labels(X, nbr_ids, q, k_out: int, labels, parts: int, speedup: float,
+                              expansion: float, seed: int, stream: int, climb: str = "eager"):
+    """Distributed search (Sec. 6, Algorithm 3) over partitions given by a
+    label per node: partition j, its nodes in id order, is searched on its own
+    subgraph -- its rows, its lists with the entries that leave it dropped --
+    with budget max(1, floor(size / speedup)) and restart stream
+    stream + j * 2^56, whose draws index its nodes in id order; of all the
+    partitions' results the k_out most similar are kept, ties to the lower
+    id.  Returns (ids, sims, summed counters, margin) as partitioned_search."""
+    X = _f32(X)
+    labels = np.asarray(labels)
+    n = labels.shape[0]
+    nbr = np.ascontiguousarray(nbr_ids[:n], dtype=np.int64)
+    ids_all, sims_all = [], []
+    tot = dict(evals=0, restarts=0, discarded=0, moves=0, draws=0)
+    margin = math.inf
+    for j in range(parts):
+        members = np.flatnonzero(labels == j)
+        if members.size == 0:
+            continue
+        local = np.full(n, -1, np.int64)
+        local[members] = np.arange(members.size)
+        lists = nbr[members]
+        inside = (lists >= 0) & (lists < n)
+        lists = np.where(inside, local[np.where(inside, lists, 0)], -1)
+        r = search(X[members], lists, q, k_out, speedup, expansion, seed,
+                   (stream + j * PART_STREAM_STEP) % (1 << 64), n=members.size, climb=climb)
+        for key in tot:
+            tot[key] += getattr(r, key)
+        margin = min(margin, r.margin)
+        ok = r.ids >= 0
+        ids_all.append(members[r.ids[ok]])
+        sims_all.append(r.sims[ok])
+    ids = np.concatenate(ids_all) if ids_all else np.empty(0, np.int64)
+    sims = np.concatenate(sims_all) if sims_all else np.empty(0)
+    order = np.lexsort((ids, -sims))
+    ids, sims = ids[order], sims[order]
+    if len(sims) > k_out:
+        a, b = sims[k_out - 1], sims[k_out]
+        if a != b:
+            margin = min(margin, abs(a - b) / max(abs(a), abs(b)))
+    out_ids = np.full(k_out, -1, np.int64)
+    out_sims = np.full(k_out, -np.inf)
+    kk = min(k_out, len(ids))
+    out_ids[:kk], out_sims[:kk] = ids[:kk], sims[:kk]
+    return out_ids, out_sims, tot, margin
+
+
+def nearest_medoid(X, rows, medoids):
+    """NearestMedoid of Algorithm 5: for each row the position of the most
+    similar medoid, sim = 1/(1 + L2) in FP64, ties to the lower position.
+    Returns (labels int32, margins float64: the relative gap between the best
+    and the second-best similarity, inf with one medoid)."""
+    X = _f32(X)
+    R = X[np.asarray(rows, dtype=np.int64)].astype(np.float64)
+    M = X[np.asarray(medoids, dtype=np.int64)].astype(np.float64)
+    sims = 1.0 / (1.0 + np.sqrt(((R[:, None, :] - M[None, :, :]) ** 2).sum(-1)))
+    labels = np.argmax(sims, axis=1).astype(np.int32)      # the first maximum: the lower position
+    if M.shape[0] == 1:
+        return labels, np.full(R.shape[0], np.inf)
+    top2 = -np.sort(-sims, axis=1)[:, :2]
+    margins = np.abs(top2[:, 0] - top2[:, 1]) / np.maximum(np.abs(top2[:, 0]), np.abs(top2[:, 1]))
+    return labels, margins
+
+
+def medoid_recompute_sizes(n_last: int, n_end: int, interval: float, batch: int = 1):
+    """Graph sizes at which the medoids are recomputed (Sec. 8, "Interval
+    between recomputing medoids"): growing by `batch` nodes at a time from
+    n_last to n_end, after every step that leaves the graph at least
+    interval * (its size at the last recompute) nodes larger than then."""
+    out, n = [], n_last
+    if interval <= 0:
+        return out
+    while n < n_end:
+        n = min(n + batch, n_end)
+        if n - n_last >= interval * n_last:
+            out.append(n)
+            n_last = n
+    return out
+
+
+def distributed_insert_stream(G: "Graph", Xnew, labels, medoids, speedup: float, expansion: float,
+                              depth: int, seed: int, interval: float, n_last: int | None = None,
+                              climb: str = "eager") -> dict:
+    """Distributed online build (Sec. 7, Algorithm 5), one new point at a
+    time on the sequential graph G: the distributed search over the label
+    partitions (restart stream = the new id), Update (Algorithm 2) over the
+    whole graph, the new node given to the partition of its nearest medoid;
+    then, when the graph has grown by interval * n_last nodes since the last
+    recompute, every non-empty partition takes the member with the smallest
+    sum of Euclidean distances to the others as its medoid (Algorithm 4's
+    update step).  labels (capacity-long int32) and medoids (int64) are
+    updated in place.  Returns per-insert margins and the recompute count."""
+    Xnew = _f32(Xnew)
+    parts = len(medoids)
+    n_last = G.n if n_last is None else n_last
+    stats = dict(search_margin=[], update_margin=[], assign_margin=[], recompute_margin=[],
+                 search_evals=[], update_evals=[], recomputes=0)
+    for x in Xnew:
+        i = G.n
+        G.X[i] = x
+        ids, sims, ctr, sm = partitioned_search_labels(G.X[:i], G.ids[:i], G.X[i], G.k, labels[:i], parts,
+                                                       speedup, expansion, seed, i, climb=climb)
+        G.ids[i], G.sims[i] = ids, sims
+        u = update(G.X, i + 1, G.ids, G.sims, i, ids, sims, depth, removed=G.removed[: i + 1])
+        lab, am = nearest_medoid(G.X, [i], medoids)
+        labels[i] = lab[0]
+        G.n = i + 1
+        stats["search_margin"].append(sm)
+        stats["update_margin"].append(u.min_margin)
+        stats["assign_margin"].append(am[0])
+        stats["search_evals"].append(ctr["evals"])
+        stats["update_evals"].append(u.evals)
+        if interval > 0 and G.n - n_last >= interval * n_last:
+            rm = math.inf
+            for j in range(parts):
+                members = np.flatnonzero(labels[: G.n] == j)
+                if members.size:
+                    medoids[j], gap = kmedoids_medoid(G.X[: G.n], members)
+                    rm = min(rm, gap)
+            stats["recompute_margin"].append(rm)
+            stats["recomputes"] += 1
+            n_last = G.n
+    stats["n_last"] = n_last
+    return stats
 
 
 def rescore(X, q, cand_ids, k_out: int):

@@ -86,6 +86,22 @@ struct knn_graph {
     int32_t climb = KNN_CLIMB_EAGER;
     cudaEvent_t ev[KNN_NUM_PHASES + 1] = {};
     bool phase_ran[KNN_NUM_PHASES] = {};
+
+    // distributed online build (Algorithm 5): partitions by label, their
+    // medoids, and the staged copy the partitioned search runs on
+    int32_t dparts = 0;              // 0: not set
+    double d_interval = 0.0;         // medoid recompute interval (fraction of n_last)
+    int64_t d_n_last = 0;            // graph size at the last recompute
+    int64_t d_recomputes = 0;
+    int32_t *d_label = nullptr;      // [cap]
+    int64_t *d_medoids = nullptr;    // [KNN_MAX_PARTS]
+    int64_t *d_order = nullptr;      // [cap] position -> node
+    int64_t *d_pos = nullptr;        // [cap] node -> position
+    int64_t *d_offsets = nullptr;    // [KNN_MAX_PARTS + 1]
+    uint8_t *d_sort = nullptr;       // counting-sort scratch
+    uint8_t *st_rows = nullptr;      // [cap][row bytes] staged searched rows
+    float *st_scale = nullptr;       // [cap] staged FP8 scales
+    int32_t *st_nbr = nullptr;       // [cap][k] staged lists
 };
 
 // Mark the start of phase `ph` (and the end of the previous one).
@@ -574,9 +590,15 @@ KNN_API knn_status knn_graph_restore(const knn_params *params, const float *vecs
     return KNN_OK;
 }
 
-KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64_t m, int64_t *out_ids,
-                                          int64_t *out_nbrs, void *stream) {
-    NvtxRange nvtx_range("knn_graph_insert_batch");
+static knn_status run_search_distributed(knn_graph *g, int64_t n0, int64_t m, cudaStream_t s,
+                                         const uint64_t **keys_out);
+static knn_status assign_partitions(knn_graph *g, int64_t n0, int64_t m, cudaStream_t s);
+
+// Algorithm 1 for a batch (knn_graph_insert_batch), or Algorithm 5 when
+// `distributed` (knn_graph_insert_distributed): the same steps but the search
+// and, after it, the new nodes' partitions.
+static knn_status insert_impl(knn_graph *g, const float *vecs, int64_t m, int64_t *out_ids, int64_t *out_nbrs,
+                              void *stream, bool distributed) {
     if (!g || !vecs) return fail(KNN_ERR_INVALID_ARG, "null argument");
     if (m < 1 || m > g->p.max_batch)
         return fail(KNN_ERR_INVALID_ARG, "m = %lld outside 1..max_batch", (long long)m);
@@ -612,7 +634,8 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     // a2-a5: iGNNS of every new point against the n0 nodes before the batch
     phase_mark(g, KNN_PHASE_SEARCH, s);
     const uint64_t *keys = nullptr;
-    knn_status sst = run_search(g, g->X + n0 * g->dp, m, K, (uint64_t)n0, s, &keys);
+    knn_status sst = distributed ? run_search_distributed(g, n0, m, s, &keys)
+                                 : run_search(g, g->X + n0 * g->dp, m, K, (uint64_t)n0, s, &keys);
     if (sst != KNN_OK) {
         // the side stream's kernel may still write cross_keys: order it
         // before anything the caller enqueues next on s
@@ -678,6 +701,7 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
     g->n = n0 + m;
     g->inserts += m;
     g->last_m = m;
+    if (distributed) TRY(assign_partitions(g, n0, m, s));
 
     if (out_ids) {
         if (is_device_ptr(out_ids)) {
@@ -698,6 +722,21 @@ KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64
         }
     }
     return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_insert_batch(knn_graph *g, const float *vecs, int64_t m, int64_t *out_ids,
+                                          int64_t *out_nbrs, void *stream) {
+    NvtxRange nvtx_range("knn_graph_insert_batch");
+    return insert_impl(g, vecs, m, out_ids, out_nbrs, stream, false);
+}
+
+KNN_API knn_status knn_graph_insert_distributed(knn_graph *g, const float *vecs, int64_t m, int64_t *out_ids,
+                                                int64_t *out_nbrs, void *stream) {
+    NvtxRange nvtx_range("knn_graph_insert_distributed");
+    if (!g) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (g->dparts < 1) return fail(KNN_ERR_INVALID_ARG, "no partitions: call knn_graph_set_partitions first");
+    if (g->n_removed > 0) return fail(KNN_ERR_UNSUPPORTED, "the distributed build takes no graph with removed nodes");
+    return insert_impl(g, vecs, m, out_ids, out_nbrs, stream, true);
 }
 
 // Replace the allocation `old` of g by `fresh` (already counted in g->bytes).
@@ -729,6 +768,7 @@ KNN_API knn_status knn_graph_reserve(knn_graph *g, int64_t capacity, int64_t hea
     if (capacity <= g->p.capacity) return KNN_OK;
     if (capacity >= (int64_t)INT32_MAX) return fail(KNN_ERR_CAPACITY, "capacity must stay below 2^31");
     if (headroom_bytes < 0) return fail(KNN_ERR_INVALID_ARG, "headroom_bytes must be >= 0");
+    if (g->d_label) return fail(KNN_ERR_UNSUPPORTED, "a graph with partitions set does not grow");
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // nothing of the graph may be in flight while its arrays move
@@ -1042,6 +1082,197 @@ KNN_API knn_status knn_graph_query_partitioned_ids(knn_graph *g, const float *ve
     NvtxRange nvtx_range("knn_graph_query_partitioned_ids");
     if (!query_ids) return fail(KNN_ERR_INVALID_ARG, "null argument");
     return query_partitioned(g, vecs, m, k_out, 0, query_ids, part_offsets, parts, out_ids, out_sims, stream);
+}
+
+// ---------------------------------------------------------------------------
+// distributed online build (Sec. 7, Algorithm 5)
+// ---------------------------------------------------------------------------
+static int64_t searched_row_bytes(const knn_graph *g) {
+    switch (g->p.storage) {
+        case KNN_STORAGE_BF16: return (int64_t)g->dp * 2;
+        case KNN_STORAGE_FP8_E4M3: return (int64_t)g->dp;
+        default: return (int64_t)g->dp * 4;
+    }
+}
+
+
+KNN_API knn_status knn_graph_set_partitions(knn_graph *g, const int32_t *labels, const int64_t *medoids,
+                                            int32_t parts, double recompute_interval, void *stream) {
+    NvtxRange nvtx_range("knn_graph_set_partitions");
+    if (!g || !labels || !medoids) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (parts < 1 || parts > KNN_MAX_PARTS || parts > g->p.max_batch)
+        return fail(KNN_ERR_UNSUPPORTED, "parts %d outside 1..min(%d, max_batch)", parts, KNN_MAX_PARTS);
+    if (!(recompute_interval >= 0.0) || !std::isfinite(recompute_interval))
+        return fail(KNN_ERR_INVALID_ARG, "recompute_interval must be finite and >= 0");
+    if (g->n_removed > 0) return fail(KNN_ERR_UNSUPPORTED, "the distributed build takes no graph with removed nodes");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    const int64_t n = g->n;
+    // check the labels and medoids on the host
+    std::vector<int32_t> lab((size_t)n);
+    std::vector<int64_t> med((size_t)parts);
+    CU(cudaMemcpyAsync(lab.data(), labels, (size_t)n * 4, cudaMemcpyDefault, s));
+    CU(cudaMemcpyAsync(med.data(), medoids, (size_t)parts * 8, cudaMemcpyDefault, s));
+    CU(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < n; ++i)
+        if (lab[(size_t)i] < 0 || lab[(size_t)i] >= parts)
+            return fail(KNN_ERR_INVALID_ARG, "label %d of node %lld outside 0..%d", lab[(size_t)i], (long long)i,
+                        parts - 1);
+    for (int32_t j = 0; j < parts; ++j)
+        if (med[(size_t)j] < 0 || med[(size_t)j] >= n)
+            return fail(KNN_ERR_INVALID_ARG, "medoid %d = %lld is not a node", j, (long long)med[(size_t)j]);
+    if (!g->d_label) {
+        // the state, sized for the capacity (the graph does not grow while set)
+        const int64_t C = g->p.capacity;
+        knn_status st = KNN_OK;
+#define DALLOC(ptr, count) \
+    if (st == KNN_OK) st = dev_alloc(g, &g->ptr, (size_t)(count));
+        DALLOC(d_label, C)
+        DALLOC(d_medoids, KNN_MAX_PARTS)
+        DALLOC(d_order, C)
+        DALLOC(d_pos, C)
+        DALLOC(d_offsets, KNN_MAX_PARTS + 1)
+        DALLOC(d_sort, kmed_sort_scratch_bytes(C, KNN_MAX_PARTS))
+        DALLOC(st_rows, C * searched_row_bytes(g))
+        if (g->p.storage == KNN_STORAGE_FP8_E4M3) { DALLOC(st_scale, C) }
+        DALLOC(st_nbr, C * g->p.k)
+#undef DALLOC
+        if (st != KNN_OK) return st;
+    }
+    CU(cudaMemcpyAsync(g->d_label, lab.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(g->d_medoids, med.data(), (size_t)parts * 8, cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    g->dparts = parts;
+    g->d_interval = recompute_interval;
+    g->d_n_last = n;
+    g->d_recomputes = 0;
+    return KNN_OK;
+}
+
+KNN_API knn_status knn_graph_get_partitions(knn_graph *g, int32_t *labels, int64_t *medoids, int64_t *recomputes,
+                                            void *stream) {
+    if (!g) return fail(KNN_ERR_INVALID_ARG, "null argument");
+    if (g->dparts < 1) return fail(KNN_ERR_INVALID_ARG, "no partitions: call knn_graph_set_partitions first");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (labels) CU(cudaMemcpyAsync(labels, g->d_label, (size_t)g->n * 4, cudaMemcpyDefault, s));
+    if (medoids) CU(cudaMemcpyAsync(medoids, g->d_medoids, (size_t)g->dparts * 8, cudaMemcpyDefault, s));
+    if (recomputes) CU(cudaMemcpyAsync(recomputes, &g->d_recomputes, 8, cudaMemcpyDefault, s));
+    CU(cudaStreamSynchronize(s));
+    return KNN_OK;
+}
+
+// The searches of Algorithm 5: Algorithm 3 over the label partitions.  Nodes
+// 0..n0-1 are staged in partition order (a stable counting sort by label, so
+// a partition keeps id order), each list keeping the entries inside its own
+// partition; every new point runs one search per partition on the staged
+// copy (the contiguous partitioned search, restart stream new id + j 2^56),
+// the candidates' positions become node ids, and the best KT of each point's
+// parts * KT candidates are kept (ties to the lower node id).
+static knn_status run_search_distributed(knn_graph *g, int64_t n0, int64_t m, cudaStream_t s,
+                                         const uint64_t **keys_out) {
+    const int P = g->dparts;
+    const int K = g->p.k;
+    const bool screening = g->p.storage != KNN_STORAGE_FP32;
+    const int KT = screening ? g->p.rescore_mult * K : K;
+    CU(launch_kmed_sort(g->d_label, n0, P, g->d_sort, g->d_order, g->d_offsets, s));
+    std::vector<int64_t> off((size_t)P + 1), live((size_t)P);
+    CU(cudaMemcpyAsync(off.data(), g->d_offsets, off.size() * 8, cudaMemcpyDeviceToHost, s));
+    CU(launch_part_stage(searched_rows(g), searched_row_bytes(g), g->p.storage == KNN_STORAGE_FP8_E4M3 ? g->scale
+                                                                                                       : nullptr,
+                         g->nbr_ids, K, g->d_label, g->d_order, g->d_pos, n0, g->st_rows, g->st_scale, g->st_nbr, s));
+    g->launches += 5;
+    CU(cudaStreamSynchronize(s));
+    int64_t largest = 0;
+    for (int q = 0; q < P; ++q) {
+        live[(size_t)q] = off[(size_t)q + 1] - off[(size_t)q];
+        largest = std::max(largest, live[(size_t)q]);
+    }
+    CU(cudaMemcpyAsync(g->part_live, live.data(), live.size() * 8, cudaMemcpyHostToDevice, s));
+    const int64_t step = std::max<int64_t>(1, g->p.max_batch / P);
+    const int64_t words = (largest + 31) / 32;
+    for (int64_t q0 = 0; q0 < m; q0 += step) {
+        const int64_t mq = std::min(step, m - q0);
+        if (!search_visited_on_chip((uint32_t)largest))
+            CU(cudaMemsetAsync(g->visited, 0, (size_t)mq * P * words * sizeof(uint32_t), s));
+        SearchArgs a{};
+        a.rows = g->st_rows;
+        a.row_scale = g->st_scale;
+        a.nbr = g->st_nbr;
+        a.removed = g->removed;  // no node is removed
+        a.queries = g->X + (size_t)(n0 + q0) * g->dp;
+        a.q_stride = g->dp;
+        a.visited = g->visited;
+        a.vwords = words;
+        a.out_keys = g->keys_search;
+        a.counters = g->counters;
+        a.totals = g->totals;
+        a.m = (int32_t)mq;
+        a.k = K;
+        a.KT = KT;
+        a.n = (uint32_t)n0;
+        a.n_live = n0;
+        a.budget = budget_of(n0, g->p.speedup);
+        a.max_draws = 64ull * (uint64_t)n0;
+        a.seed = g->p.seed;
+        a.stream_base = (uint64_t)(n0 + q0);
+        const double e = g->p.expansion;
+        a.discard = (e > 0.0 && std::isfinite(e)) ? 1 : 0;
+        a.expansion = a.discard ? (float)e : 1.0f;
+        a.climb = g->climb;
+        a.parts = P;
+        a.part_off = g->d_offsets;
+        a.part_live = g->part_live;
+        a.speedup = g->p.speedup;
+        a.vis_n = (uint32_t)largest;
+        CU(launch_search(g->p.storage, g->dp, a, s));
+        CU(launch_part_keys_to_nodes(g->keys_search, mq * P * KT, g->d_order, s));
+        CU(launch_merge_parts(g->keys_search, (int32_t)mq, P, KT, g->keys_merge + (size_t)q0 * KT, g->counters,
+                              g->counters_q + (size_t)q0 * NCTR, s));
+        g->launches += 3;
+    }
+    // per new point, the sums over its parts, where Update adds its own count
+    CU(cudaMemcpyAsync(g->counters, g->counters_q, (size_t)m * NCTR * sizeof(long long), cudaMemcpyDeviceToDevice,
+                       s));
+    g->last_counters_src = g->counters;
+    g->phase_ran[KNN_PHASE_SEARCH] = true;
+    phase_mark(g, KNN_PHASE_RESCORE, s);
+    if (!screening) {
+        *keys_out = g->keys_merge;
+        return KNN_OK;
+    }
+    RescoreArgs r{};
+    r.rows = g->X;
+    r.queries = g->X + (size_t)n0 * g->dp;
+    r.q_stride = g->dp;
+    r.cand_keys = g->keys_merge;
+    r.out_keys = g->keys_final;
+    r.totals = g->totals;
+    r.m = (int32_t)m;
+    r.KT = KT;
+    r.k_out = K;
+    CU(launch_rescore(g->dp, r, s));
+    ++g->launches;
+    g->phase_ran[KNN_PHASE_RESCORE] = true;
+    *keys_out = g->keys_final;
+    return KNN_OK;
+}
+
+// After a distributed batch: nodes n0 .. n0+m-1 go to the partition of their
+// nearest medoid; then, when the graph has grown by d_interval * d_n_last
+// since the last recompute, every non-empty partition takes a new medoid.
+static knn_status assign_partitions(knn_graph *g, int64_t n0, int64_t m, cudaStream_t s) {
+    CU(launch_part_nearest(g->X, g->dp, g->X + (size_t)n0 * g->dp, m, g->d_medoids, g->dparts, g->d_label + n0, s));
+    ++g->launches;
+    if (g->d_interval > 0.0 && (double)(g->n - g->d_n_last) >= g->d_interval * (double)g->d_n_last) {
+        CU(launch_kmed_sort(g->d_label, g->n, g->dparts, g->d_sort, g->d_order, g->d_offsets, s));
+        CU(launch_kmed_update(g->dp, g->X, g->d_order, g->d_offsets, g->dparts, g->d_medoids, s));
+        g->launches += 4;
+        g->d_n_last = g->n;
+        ++g->d_recomputes;
+    }
+    return KNN_OK;
 }
 
 KNN_API knn_status knn_graph_remove(knn_graph *g, const int64_t *ids, int64_t m, void *stream) {

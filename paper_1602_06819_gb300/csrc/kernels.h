@@ -247,6 +247,18 @@ cudaError_t launch_kmed_sort(const int32_t *labels, int64_t n, int p, void *scra
 cudaError_t launch_kmed_update(int dp, const float *X, const int64_t *order, const int64_t *offsets, int p,
                                int64_t *medoids, cudaStream_t s);
 
+// distributed online build (partition.cu): staged copy of nodes 0..n-1 in
+// partition order (pos = inverse of order; rows of row_bytes, a multiple of
+// 16; scale nullable; list entries outside a node's partition -> -1)
+cudaError_t launch_part_stage(const uint8_t *rows, int64_t row_bytes, const float *scale, const int32_t *nbr, int k,
+                              const int32_t *label, const int64_t *order, int64_t *pos, int64_t n, uint8_t *st_rows,
+                              float *st_scale, int32_t *st_nbr, cudaStream_t s);
+// candidate keys of a staged search: position ids -> node ids (in place)
+cudaError_t launch_part_keys_to_nodes(uint64_t *keys, int64_t count, const int64_t *order, cudaStream_t s);
+// labels[i] = position of the medoid nearest to rows[i] (ties to the lower)
+cudaError_t launch_part_nearest(const float *X, int dp, const float *rows, int64_t m, const int64_t *medoids, int p,
+                                int32_t *labels, cudaStream_t s);
+
 // shape of a graph for the server (graph.cu)
 struct GraphShape {
     int dim, k, max_batch;

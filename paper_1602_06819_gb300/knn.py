@@ -48,6 +48,7 @@ EXPORTED = ("knn_graph_create", "knn_graph_restore", "knn_graph_insert_batch", "
             "knn_graph_query_ids", "knn_graph_query_partitioned", "knn_graph_query_partitioned_ids",
             "knn_graph_remove", "knn_graph_get_edges",
             "knn_graph_reserve",
+            "knn_graph_set_partitions", "knn_graph_insert_distributed", "knn_graph_get_partitions",
             "knn_graph_last_counters",
             "knn_graph_set_timing", "knn_graph_last_timing", "knn_graph_set_search", "knn_graph_stats",
             "knn_graph_destroy", "knn_exact_graph", "knn_exact_set_path", "knn_exact_last_info",
@@ -136,6 +137,9 @@ def _load_library() -> ctypes.CDLL:
         "knn_graph_query_partitioned_ids": (I32, [P, P, I64, I32, P, P, I32, P, P, P]),
         "knn_graph_remove": (I32, [P, P, I64, P]),
         "knn_graph_reserve": (I32, [P, I64, I64, P]),
+        "knn_graph_set_partitions": (I32, [P, P, P, I32, ctypes.c_double, P]),
+        "knn_graph_insert_distributed": (I32, [P, P, I64, P, P, P]),
+        "knn_graph_get_partitions": (I32, [P, P, P, P, P]),
         "knn_graph_get_edges": (I32, [P, P, P, I64, ctypes.POINTER(I64), P]),
         "knn_graph_last_counters": (I32, [P, P, I64, P]),
         "knn_graph_set_timing": (I32, [P, I32]),
@@ -282,6 +286,34 @@ def knn_graph_query_partitioned_ids(g, vecs, k_out: int, query_ids, part_offsets
                                                _ptr(part_offsets), part_offsets.shape[0] - 1,
                                                _ptr(out_ids), _ptr(out_sims), _stream(stream)),
            "knn_graph_query_partitioned_ids")
+
+
+def knn_graph_set_partitions(g, labels, medoids, recompute_interval: float = 0.0, stream=None) -> None:
+    """Algorithm 5's partitions: labels (int32 [n]) and medoids (int64 [parts])."""
+    _check_dtype(labels, "int32", "labels")
+    _check_dtype(medoids, "int64", "medoids")
+    _check(lib.knn_graph_set_partitions(g, _ptr(labels), _ptr(medoids), medoids.shape[0], float(recompute_interval),
+                                        _stream(stream)), "knn_graph_set_partitions")
+
+
+def knn_graph_insert_distributed(g, vecs, out_ids=None, out_nbrs=None, stream=None) -> None:
+    """Algorithm 5 for a batch: the distributed search, Update, nearest medoid."""
+    _check_dtype(vecs, "float32", "vecs")
+    _check_dtype(out_ids, "int64", "out_ids")
+    _check_dtype(out_nbrs, "int64", "out_nbrs")
+    _check(lib.knn_graph_insert_distributed(g, _ptr(vecs), vecs.shape[0], _ptr(out_ids), _ptr(out_nbrs),
+                                            _stream(stream)), "knn_graph_insert_distributed")
+
+
+def knn_graph_get_partitions(g, labels=None, medoids=None, stream=None) -> int:
+    """Fills labels (int32 [n]) and medoids (int64 [parts]); returns the
+    number of medoid recomputes so far."""
+    _check_dtype(labels, "int32", "labels")
+    _check_dtype(medoids, "int64", "medoids")
+    rec = ctypes.c_int64()
+    _check(lib.knn_graph_get_partitions(g, _ptr(labels), _ptr(medoids), ctypes.addressof(rec), _stream(stream)),
+           "knn_graph_get_partitions")
+    return rec.value
 
 
 def knn_graph_remove(g, ids, stream=None) -> None:
@@ -448,6 +480,15 @@ class Graph:
 
     def remove(self, ids, stream=None):
         knn_graph_remove(self.handle, ids, stream)
+
+    def set_partitions(self, labels, medoids, recompute_interval: float = 0.0, stream=None):
+        knn_graph_set_partitions(self.handle, labels, medoids, recompute_interval, stream)
+
+    def insert_distributed(self, vecs, out_ids=None, out_nbrs=None, stream=None):
+        knn_graph_insert_distributed(self.handle, vecs, out_ids, out_nbrs, stream)
+
+    def partitions(self, labels=None, medoids=None, stream=None) -> int:
+        return knn_graph_get_partitions(self.handle, labels, medoids, stream)
 
     def reserve(self, capacity: int, headroom_bytes: int = 0, stream=None):
         knn_graph_reserve(self.handle, capacity, headroom_bytes, stream)

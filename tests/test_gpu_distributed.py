@@ -1,0 +1,202 @@
+"""Distributed online build (Sec. 7, Algorithm 5) on the GPU against the oracle.
+
+* One partition: knn_graph_insert_distributed is knn_graph_insert_batch, bit
+  for bit (FP32 and BF16 screening).
+* One point per call over three k-medoids partitions with a 10 % medoid
+  recompute interval: the whole graph, the new node's list and counters, the
+  partition labels and the medoids equal the sequential oracle's after every
+  insert, up to the first insert whose decisions the oracle flags as a near
+  tie.
+* Batches: the edge recall against the exact graph is within 0.01 of the
+  oracle's sequential distributed build on the same stream.
+* Errors: no partitions, labels or medoids out of range, growth or removal
+  while partitions are set.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import cuda_tensor, gather_tol, rel_err
+from paper_1602_06819_gb300.inputs import Mixture
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def knn():
+    from paper_1602_06819_gb300 import build
+    build.build()
+    from paper_1602_06819_gb300 import knn as module
+    return module
+
+
+def make_graph(knn, X0, k, speedup, expansion, seed, capacity, max_batch, depth=2, storage=0, nbr_ids=None):
+    cfg = knn.GraphConfig(dim=X0.shape[1], k=k, depth=depth, storage=storage, speedup=speedup,
+                          expansion=expansion, rescore_mult=4, max_batch=max_batch, seed=seed,
+                          capacity=capacity)
+    return knn.Graph(cfg, cuda_tensor(X0), nbr_ids=None if nbr_ids is None else cuda_tensor(nbr_ids))
+
+
+def edges(g, n, k):
+    import torch
+    ids = torch.empty((n, k), dtype=torch.int64, device="cuda")
+    sims = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    assert g.edges(ids, sims) == n
+    return ids.cpu().numpy(), sims.cpu().numpy()
+
+
+def partitions(g, n, parts):
+    labels = np.empty(n, np.int32)
+    medoids = np.empty(parts, np.int64)
+    rec = g.partitions(labels, medoids)
+    return labels, medoids, rec
+
+
+def _recall(ids, exact):
+    return oracle.correct_edges(ids, exact) / exact.size
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_one_partition_is_the_batch_insert(knn, storage):
+    mix = Mixture(d=32, components=8, half_width=10.0, sigma=1.0, seed=31)
+    X0, Xs = mix.sample(3000, 1), mix.sample(4 * 96, 2)
+    k = 10
+    a = make_graph(knn, X0, k, 4.0, 5.0, 7, 3000 + len(Xs), 96, storage=storage)
+    b = make_graph(knn, X0, k, 4.0, 5.0, 7, 3000 + len(Xs), 96, storage=storage)
+    try:
+        b.set_partitions(np.zeros(3000, np.int32), np.array([0], np.int64), 0.1)
+        ca, cb = np.empty((96, 8), np.int64), np.empty((96, 8), np.int64)
+        for b0 in range(0, len(Xs), 96):
+            a.insert(cuda_tensor(Xs[b0:b0 + 96]))
+            a.counters(ca)
+            b.insert_distributed(cuda_tensor(Xs[b0:b0 + 96]))
+            b.counters(cb)
+            assert np.array_equal(ca, cb)
+        ia, sa = edges(a, 3000 + len(Xs), k)
+        ib, sb = edges(b, 3000 + len(Xs), k)
+        labels, medoids, rec = partitions(b, 3000 + len(Xs), 1)
+    finally:
+        a.close()
+        b.close()
+    assert np.array_equal(ia, ib) and np.array_equal(sa, sb)
+    assert not labels.any() and rec == len(oracle.medoid_recompute_sizes(3000, 3000 + len(Xs), 0.1, batch=96))
+    assert rec == 1 and medoids[0] >= 0                # 3,384 nodes pass 10 % of 3,000
+
+
+def test_single_point_inserts_match_oracle(knn):
+    """Both sides start from the oracle's exact graph of 800 points (d = 16)
+    split in three balanced k-medoids partitions; 120 points are inserted
+    one at a time with a 10 % recompute interval (one recompute, at 880)."""
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=32)
+    n0, na, k, parts = 800, 120, 10, 3
+    speedup, e, seed, depth, interval = 4.0, 5.0, 5, 2, 0.1
+    X0, Xs = mix.sample(n0, 1), mix.sample(na, 2)
+    og = oracle.Graph.exact(X0, k, capacity=n0 + na)
+    lab0, med, _ = oracle.kmedoids(X0, parts, imbalance=1.1, chunks=1, iters=2, seed=6)
+    labels = np.zeros(n0 + na, np.int32)
+    labels[:n0] = lab0
+    medoids = med.copy()
+    tol = gather_tol(16)
+    # one point a call; max_batch bounds the searches of a launch, parts per point
+    g = make_graph(knn, X0, k, speedup, e, seed, n0 + na, parts, depth, nbr_ids=og.ids[:n0])
+    compared, n_last, recomputes = 0, n0, 0
+    try:
+        g.set_partitions(lab0.copy(), med.copy(), interval)
+        ctr = np.empty((1, 8), np.int64)
+        import torch
+        for i in range(na):
+            new = n0 + i
+            st = oracle.distributed_insert_stream(og, Xs[i:i + 1], labels, medoids, speedup, e, depth, seed,
+                                                  interval, n_last=n_last)
+            n_last = st["n_last"]
+            recomputes += st["recomputes"]
+            margins = st["search_margin"] + st["update_margin"] + st["assign_margin"] + st["recompute_margin"]
+            ambiguous = min(margins) < tol
+            nbrs = torch.empty((1, k), dtype=torch.int64)
+            g.insert_distributed(cuda_tensor(Xs[i:i + 1]), None, nbrs)
+            g.counters(ctr)
+            got_ids, got_sims = edges(g, new + 1, k)
+            g_labels, g_medoids, g_rec = partitions(g, new + 1, parts)
+            same = (list(nbrs[0].numpy()) == list(og.ids[new]) and ctr[0, 0] == st["search_evals"][0]
+                    and ctr[0, 1] == st["update_evals"][0] and np.array_equal(got_ids, og.ids[:new + 1])
+                    and np.array_equal(g_labels, labels[:new + 1]) and np.array_equal(g_medoids, medoids)
+                    and g_rec == recomputes)
+            if not same:
+                assert ambiguous, f"insert {i} differs from the oracle without a near tie"
+                break
+            assert rel_err(got_sims, og.sims[:new + 1]).max() <= 1e-5
+            compared += 1
+    finally:
+        g.close()
+    print(f"distributed build, 3 partitions: {compared} of {na} single-point inserts equal the oracle")
+    assert compared >= 60 and recomputes >= (1 if compared == na else 0)
+
+
+def test_batched_recall_matches_sequential_distributed(knn):
+    """4,000 initial points in four k-medoids partitions, 2,048 inserted in
+    batches of 128 with a 10 % recompute interval."""
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=33)
+    n0, na, B, k, parts = 4000, 2048, 128, 10, 4
+    speedup, e, seed, depth, interval = 4.0, 5.0, 8, 2, 0.1
+    X0, Xs = mix.sample(n0, 1), mix.sample(na, 2)
+    X = np.vstack([X0, Xs])
+    exact, _, _ = oracle.exact_knn(X, k)
+    og = oracle.Graph.exact(X0, k, capacity=n0 + na)
+    start = og.ids[:n0].copy()
+    lab0, med, _ = oracle.kmedoids(X0, parts, imbalance=1.1, chunks=1, iters=2, seed=9)
+    labels = np.zeros(n0 + na, np.int32)
+    labels[:n0] = lab0
+    st = oracle.distributed_insert_stream(og, Xs, labels, med.copy(), speedup, e, depth, seed, interval)
+    r_seq = _recall(og.ids, exact)
+    g = make_graph(knn, X0, k, speedup, e, seed, n0 + na, B, depth, nbr_ids=start)
+    try:
+        g.set_partitions(lab0.copy(), med.copy(), interval)
+        for b0 in range(0, na, B):
+            g.insert_distributed(cuda_tensor(Xs[b0:b0 + B]))
+        got, sims = edges(g, n0 + na, k)
+        g_labels, _, g_rec = partitions(g, n0 + na, parts)
+    finally:
+        g.close()
+    r_gpu = _recall(got, exact)
+    print(f"distributed build, batches of {B}: edge recall {r_gpu:.4f} (sequential oracle {r_seq:.4f}); "
+          f"medoid recomputes {g_rec} (oracle {st['recomputes']})")
+    assert abs(r_gpu - r_seq) <= 0.01, (r_gpu, r_seq)
+    assert g_rec == len(oracle.medoid_recompute_sizes(n0, n0 + na, interval, batch=B))
+    assert g_labels.min() >= 0 and g_labels.max() < parts and np.array_equal(g_labels[:n0], lab0)
+    assert got.min() >= 0 and not np.any(got == np.arange(n0 + na)[:, None])
+    assert np.all(np.diff(sims, axis=1) <= 0)
+
+
+def test_distributed_errors(knn):
+    mix = Mixture(d=16, components=4, half_width=10.0, sigma=1.0, seed=34)
+    X0 = mix.sample(500, 1)
+    g = make_graph(knn, X0, 8, 4.0, 5.0, 1, 700, 64)
+    try:
+        with pytest.raises(knn.KnnError) as ei:
+            g.insert_distributed(cuda_tensor(mix.sample(4, 2)))
+        assert ei.value.status == knn.KNN_ERR_INVALID_ARG
+        bad = np.zeros(500, np.int32)
+        bad[17] = 3
+        with pytest.raises(knn.KnnError) as ei:
+            g.set_partitions(bad, np.array([0, 1, 2], np.int64))
+        assert ei.value.status == knn.KNN_ERR_INVALID_ARG
+        with pytest.raises(knn.KnnError) as ei:
+            g.set_partitions(np.zeros(500, np.int32), np.array([500], np.int64))
+        assert ei.value.status == knn.KNN_ERR_INVALID_ARG
+        with pytest.raises(knn.KnnError) as ei:
+            g.set_partitions(np.zeros(500, np.int32), np.zeros(65, np.int64))
+        assert ei.value.status == knn.KNN_ERR_UNSUPPORTED
+        g.set_partitions((np.arange(500) % 2).astype(np.int32), np.array([0, 1], np.int64))
+        g.insert_distributed(cuda_tensor(mix.sample(64, 3)))
+        labels, medoids, rec = partitions(g, 564, 2)
+        assert set(np.unique(labels[500:])) <= {0, 1} and rec == 0 and medoids.tolist() == [0, 1]
+        with pytest.raises(knn.KnnError) as ei:
+            g.reserve(2000)
+        assert ei.value.status == knn.KNN_ERR_UNSUPPORTED
+        import torch
+        g.remove(torch.as_tensor([3], dtype=torch.int64))
+        with pytest.raises(knn.KnnError) as ei:
+            g.insert_distributed(cuda_tensor(mix.sample(4, 4)))
+        assert ei.value.status == knn.KNN_ERR_UNSUPPORTED
+    finally:
+        g.close()

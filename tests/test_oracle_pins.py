@@ -566,6 +566,134 @@ def test_partitioned_search_does_not_leave_its_part(orc):
     assert np.all(ids < 100)
 
 
+# ---------------------------------------------------------------------------
+# partitions by label (Algorithm 3) and the distributed online build
+# (Sec. 7, Algorithm 5)
+# ---------------------------------------------------------------------------
+
+def test_partitioned_search_labels_one_part_is_the_search(orc):
+    mix = Mixture(d=8, components=5, half_width=5.0, sigma=1.0, seed=13)
+    X = mix.sample(400, 1)
+    nbr, _, _ = orc.exact_knn(X, 6)
+    for i, q in enumerate(mix.sample(5, 2)):
+        ids, sims, tot, _ = orc.partitioned_search_labels(X, nbr, q, 5, np.zeros(400, np.int32), 1, 4.0, 5.0,
+                                                          seed=2, stream=i)
+        r = orc.search(X, nbr, q, 5, 4.0, 5.0, seed=2, stream=i)
+        assert list(ids) == list(r.ids) and tot["evals"] == r.evals and tot["moves"] == r.moves
+
+
+def test_partitioned_search_labels_exhaustive(orc):
+    """speedup 1 without the expansion test evaluates every node of every
+    partition, so the merged list is the exact k nearest whatever the
+    (scattered) labels."""
+    mix = Mixture(d=8, components=5, half_width=5.0, sigma=1.0, seed=14)
+    X = mix.sample(500, 1)
+    nbr, _, _ = orc.exact_knn(X, 6)
+    labels = np.random.default_rng(1).integers(0, 4, 500).astype(np.int32)
+    Xd = X.astype(np.float64)
+    for i, q in enumerate(mix.sample(6, 2)):
+        ids, _, tot, _ = orc.partitioned_search_labels(X, nbr, q, 8, labels, 4, 1.0, math.inf, seed=1, stream=i)
+        s = 1.0 / (1.0 + np.linalg.norm(Xd - q.astype(np.float64), axis=1))
+        assert list(ids) == list(np.lexsort((np.arange(500), -s))[:8])
+        assert tot["evals"] == 500
+
+
+def test_partitioned_search_labels_draw_streams(orc):
+    """With a budget of one similarity per partition, partition j evaluates
+    its member of position draw(key(seed, s + j 2^56), 0, size_j), its members
+    taken in id order."""
+    X = Mixture(d=4, components=3, half_width=5.0, sigma=1.0, seed=15).sample(300, 1)
+    nbr, _, _ = orc.exact_knn(X, 4)
+    labels = (np.arange(300) * 7 % 3).astype(np.int32)
+    q = X[7] + 0.1
+    s0 = 42
+    ids, _, tot, _ = orc.partitioned_search_labels(X, nbr, q, 3, labels, 3, 1000.0, 5.0, seed=9, stream=s0)
+    want = []
+    for j in range(3):
+        members = np.flatnonzero(labels == j)
+        want.append(members[orc.draw(orc.search_key(9, s0 + j * (1 << 56)), 0, members.size)])
+    assert sorted(ids.tolist()) == sorted(want) and tot["evals"] == 3
+
+
+def test_partitioned_search_labels_is_the_contiguous_search_renumbered(orc):
+    """Renumbering the nodes partition by partition (id order within each)
+    turns the label partitions into contiguous ones: the two searches agree."""
+    mix = Mixture(d=6, components=6, half_width=6.0, sigma=1.0, seed=16)
+    X = mix.sample(600, 1)
+    nbr, _, _ = orc.exact_knn(X, 8)
+    labels = np.random.default_rng(2).integers(0, 5, 600).astype(np.int32)
+    perm = np.lexsort((np.arange(600), labels))            # new position -> node
+    pos = np.empty(600, np.int64)
+    pos[perm] = np.arange(600)
+    Xp = X[perm]
+    nbr_p = pos[nbr[perm]]
+    offs = np.concatenate([[0], np.cumsum(np.bincount(labels, minlength=5))])
+    for i, q in enumerate(mix.sample(8, 3)):
+        a = orc.partitioned_search_labels(X, nbr, q, 10, labels, 5, 4.0, 5.0, seed=4, stream=i)
+        b = orc.partitioned_search(Xp, nbr_p, q, 10, offs, 4.0, 5.0, seed=4, stream=i)
+        assert list(a[0]) == list(perm[b[0]]) and a[2] == b[2]
+
+
+def test_nearest_medoid_hand_example(orc):
+    """1-D points 0, 1, 4, 5, 10 with medoids at nodes 0 (x = 0) and 4
+    (x = 10): 4 is nearer 0 than 10; 5 lies halfway, and the tie goes to the
+    lower position."""
+    X = np.array([[0.0], [1.0], [4.0], [5.0], [10.0]], np.float32)
+    labels, margins = orc.nearest_medoid(X, [0, 1, 2, 3, 4], [0, 4])
+    assert labels.tolist() == [0, 0, 0, 0, 1]
+    assert margins[3] == 0.0 and margins[2] > 0.0
+    labels, margins = orc.nearest_medoid(X, [3], [4, 0])       # medoid order decides the tie
+    assert labels.tolist() == [0]
+
+
+def test_medoid_recompute_sizes_paper_example(orc):
+    for ln in read_golden("medoid_interval.txt"):
+        n_last, interval, n_end, *sizes = ln.split()
+        got = orc.medoid_recompute_sizes(int(n_last), int(n_end), float(interval))
+        assert got == [int(v) for v in sizes]
+    assert orc.medoid_recompute_sizes(4000, 8000, 0.0) == []
+    # batches of 1,000: the first batch already passes 10 %
+    assert orc.medoid_recompute_sizes(4000, 8000, 0.1, batch=1000) == [5000, 6000, 7000, 8000]
+
+
+def test_distributed_build_one_partition_is_algorithm_1(orc):
+    """One partition and no recompute: Algorithm 5 is Algorithm 1."""
+    mix = Mixture(d=8, components=6, half_width=8.0, sigma=1.0, seed=17)
+    X0, Xs = mix.sample(500, 1), mix.sample(60, 2)
+    a = orc.Graph.exact(X0, 6, capacity=560)
+    b = orc.Graph.exact(X0, 6, capacity=560)
+    a.insert_stream(Xs, 4.0, 5.0, 2, seed=3)
+    labels = np.zeros(560, np.int32)
+    st = orc.distributed_insert_stream(b, Xs, labels, np.array([0], np.int64), 4.0, 5.0, 2, 3, 0.0)
+    assert np.array_equal(a.ids, b.ids) and np.array_equal(a.sims, b.sims)
+    assert st["recomputes"] == 0 and not labels.any()
+
+
+def test_distributed_build_assigns_and_recomputes(orc):
+    """Three partitions, 10 % interval: new nodes go to their nearest medoid;
+    the recompute count follows the schedule, and after the last recompute
+    every medoid is the member with the smallest sum of distances (scipy)."""
+    mix = Mixture(d=4, components=3, half_width=8.0, sigma=1.0, seed=18)
+    X0 = mix.sample(300, 1)
+    Xs = mix.sample(63, 2)                                      # 300 -> 330 -> 363: two recomputes
+    g = orc.Graph.exact(X0, 5, capacity=363)
+    labels0, medoids, _ = orc.kmedoids(X0, 3, imbalance=1.1, chunks=1, iters=2, seed=4)
+    labels = np.zeros(363, np.int32)
+    labels[:300] = labels0
+    med_before = medoids.copy()
+    st = orc.distributed_insert_stream(g, Xs, labels, medoids, 4.0, 5.0, 2, 5, 0.1)
+    assert orc.medoid_recompute_sizes(300, 363, 0.1) == [330, 363]
+    assert st["recomputes"] == 2
+    # inserts 300..329 were assigned with the initial medoids
+    want, _ = orc.nearest_medoid(g.X, np.arange(300, 330), med_before)
+    assert np.array_equal(labels[300:330], want)
+    D = cdist(g.X[:363].astype(np.float64), g.X[:363].astype(np.float64))
+    for j in range(3):
+        members = np.flatnonzero(labels == j)
+        sums = D[np.ix_(members, members)].sum(1)
+        assert medoids[j] == members[np.argmin(sums)]
+
+
 def test_sequential_recall_fixture_is_consistent(orc):
     """tests/golden/sequential_recall_d128.txt (written by the oracle's
     sequential build, Algorithm 1, on the d = 128 workload) against what its
