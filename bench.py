@@ -62,7 +62,8 @@ def parse_args():
                     help="store the initial points in the order of their balanced k-medoids "
                          "clusters (Algorithm 4; n/1000 clusters) before building the graph")
     ap.add_argument("--experiment", default=None,
-                    choices=("search", "depth", "partitions", "serving", "batching", "tail", "growth"),
+                    choices=("search", "depth", "partitions", "serving", "batching", "tail", "growth",
+                             "distributed"),
                     help="instead of the benchmark line: the search sweeps (expansion e; "
                          "iGNNS against GNNS at equal evaluations) or the DEPTH sweep, "
                          "one JSON line per point")
@@ -625,6 +626,78 @@ def run_depth_experiment(knn, torch, np):
                       update_evals_per_insert=update, inserts_per_s=na / secs)
 
 
+def run_distributed_experiment(knn, torch, np):
+    """The distributed online build (Algorithm 5) on synthetic R^3 data (a
+    10-component Gaussian mixture), one point inserted at a time, k = 10,
+    speedup 4, e = 5, DEPTH 2, 8 balanced k-medoids partitions of the
+    initial points:
+    (1) the interval between medoid recomputes (Sec. 8): 4,000 initial
+        points + 4,000 added, medoids recomputed at every 10 % of growth or
+        never, 10 repetitions; correct edges e_c of the final graph;
+    (2) graph quality (Sec. 8.5's experiment): 8,000 + 16,000, e_c and Q
+        against the exact graph of the points so far every 4,000 inserts,
+        beside Algorithm 1 (one partition) on the same stream."""
+    from paper_1602_06819_gb300 import inputs
+    k, P, speedup, e = 10, 8, 4.0, 5.0
+
+    def build(X0, Xs, interval, parts, seed, checkpoints=()):
+        n0, na = X0.shape[0], Xs.shape[0]
+        cfg = knn.GraphConfig(dim=X0.shape[1], k=k, depth=2, speedup=speedup, expansion=e,
+                              max_batch=max(parts, 1), seed=seed, capacity=n0 + na)
+        g = knn.Graph(cfg, X0)
+        labels = torch.empty(n0, dtype=torch.int32, device="cuda")
+        medoids = torch.empty(parts, dtype=torch.int64, device="cuda")
+        knn.knn_balanced_kmedoids(X0, parts, 1.1, 8, 2, seed, labels, medoids)
+        g.set_partitions(labels, medoids, interval)
+        marks = []
+        t0 = time.perf_counter()
+        for i in range(na):
+            g.insert_distributed(Xs[i:i + 1])
+            if i + 1 in checkpoints:
+                n = n0 + i + 1
+                online = torch.empty((n, k), dtype=torch.int64, device="cuda")
+                g.edges(online)
+                exact = torch.empty((n, k), dtype=torch.int64, device="cuda")
+                knn.knn_exact_graph(torch.cat([X0, Xs[:i + 1]]), k, exact)
+                e_c = edge_recall(torch, online, exact)
+                marks.append({"added": i + 1, "e_c": e_c, "edge_recall": e_c / exact.numel(),
+                              "Q": quality_q(e_c, n0, i + 1, k)})
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        online = torch.empty((n0 + na, k), dtype=torch.int64, device="cuda")
+        g.edges(online)
+        rec = g.partitions()
+        g.close()
+        return online, rec, marks, na / secs
+
+    mix = inputs.Mixture(d=3, components=10, half_width=10.0, sigma=1.0, seed=41)
+    # (1) recompute interval
+    for interval in (0.1, 0.0):
+        ecs, recs = [], []
+        for rep in range(10):
+            X0 = torch.from_numpy(mix.sample(4000, 100 + rep)).cuda()
+            Xs = torch.from_numpy(mix.sample(4000, 200 + rep)).cuda()
+            exact = torch.empty((8000, k), dtype=torch.int64, device="cuda")
+            knn.knn_exact_graph(torch.cat([X0, Xs]), k, exact)
+            online, rec, _, rate = build(X0, Xs, interval, P, 300 + rep)
+            ecs.append(edge_recall(torch, online, exact))
+            recs.append(rec)
+        _exp_line(experiment="distributed", study="medoid_interval", set="gmm-d3-4000+4000", parts=P, k=k,
+                  speedup=speedup, expansion=e, interval=interval, repetitions=10,
+                  e_c_mean=float(np.mean(ecs)), e_c_std=float(np.std(ecs)), e_c_min=int(min(ecs)),
+                  e_c_max=int(max(ecs)), edge_recall_mean=float(np.mean(ecs)) / (8000 * k),
+                  recomputes=int(recs[0]), inserts_per_s=rate)
+    # (2) graph quality over time, beside Algorithm 1
+    X0 = torch.from_numpy(mix.sample(8000, 1)).cuda()
+    Xs = torch.from_numpy(mix.sample(16000, 2)).cuda()
+    marks_at = (4000, 8000, 12000, 16000)
+    for parts in (P, 1):
+        _, rec, marks, rate = build(X0, Xs, 0.0, parts, 7, marks_at)
+        for mk in marks:
+            _exp_line(experiment="distributed", study="quality", set="gmm-d3-8000+16000", parts=parts, k=k,
+                      speedup=speedup, expansion=e, **mk, inserts_per_s=rate)
+
+
 def run_partition_experiment(knn, torch, np):
     """Partitioned search (Algorithm 3) on the default workload's 100,000
     initial points stored in the order of P balanced k-medoids clusters:
@@ -976,7 +1049,7 @@ def main():
         {"search": run_search_experiment, "depth": run_depth_experiment,
          "partitions": run_partition_experiment, "serving": run_serving_experiment,
          "batching": run_batching_experiment, "tail": run_tail_experiment,
-         "growth": run_growth_experiment}[args.experiment](
+         "growth": run_growth_experiment, "distributed": run_distributed_experiment}[args.experiment](
             knn, torch, np)
         return
 
