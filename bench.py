@@ -421,11 +421,12 @@ def run_precision_record(knn, torch, np, hbm_peak, peak_src, steps=20, warmup=3)
     """The precision workload (1,000,000 initial points, d = 96, 1,000
     components, k = 20), one graph per searched copy: FP32, BF16 and
     FP8-E4M3 screening with an FP32 re-score of the best 4k candidates.  Per
-    form: 1,024-point insert batches timed as the main line times them (L2
-    flushed between steps), the search kernel's roofline, the edge recall of
-    the inserted points' lists against the exact graph, and the similarity
-    error against FP64 (numpy, on sampled pairs): of the lists' FP32
-    similarities, and of the screening copy's similarities."""
+    form: insert batches of the workload's size (4,096 points) timed as the
+    main line times them (L2 flushed between steps), the search kernel's
+    roofline, the edge recall of the inserted points' lists against the
+    exact graph, and the similarity error against FP64 (numpy, on sampled
+    pairs): of the lists' FP32 similarities, and of the screening copy's
+    similarities."""
     from paper_1602_06819_gb300 import inputs
     W = inputs.PRECISION_D96
     n0, B, k, d = W.n_init, W.batch, W.k, W.mixture.d
@@ -1001,20 +1002,21 @@ def run_tail_experiment(knn, torch, np):
     from paper_1602_06819_gb300 import inputs
     names = ("search_evals", "update_evals", "restarts", "discarded", "moves", "adjacency_reads",
              "draws")
+    B = 1024  # insert batches of 1,024 on both workloads
     for W, storage in ((inputs.PLAIN_D128, knn.KNN_STORAGE_FP32),
                        (inputs.PRECISION_D96, knn.KNN_STORAGE_BF16)):
         X0 = torch.from_numpy(W.initial()).cuda()
-        Xs = torch.from_numpy(W.mixture.sample(3 * W.batch, W.seed_stream)).cuda()
+        Xs = torch.from_numpy(W.mixture.sample(3 * B, W.seed_stream)).cuda()
         Q = torch.from_numpy(W.queries(1024)).cuda()
         cfg = knn.GraphConfig(dim=W.mixture.d, k=W.k, depth=2, storage=storage, speedup=4.0,
-                              expansion=W.expansion, rescore_mult=4, max_batch=W.batch,
-                              seed=W.seed_search, capacity=W.n_init + 3 * W.batch)
+                              expansion=W.expansion, rescore_mult=4, max_batch=B,
+                              seed=W.seed_search, capacity=W.n_init + 3 * B)
         g = knn.Graph(cfg, X0)
         g.set_timing(True)
         for i in range(3):
-            g.insert(Xs[i * W.batch:(i + 1) * W.batch])
+            g.insert(Xs[i * B:(i + 1) * B])
         search_ms = g.last_timing()["search"]
-        ctr = np.empty((W.batch, 8), np.int64)
+        ctr = np.empty((B, 8), np.int64)
         g.counters(ctr)
         pct = {nm: [int(np.percentile(ctr[:, c], p)) for p in (0, 50, 90, 99, 100)]
                for c, nm in enumerate(names)}
@@ -1025,8 +1027,8 @@ def run_tail_experiment(knn, torch, np):
             g.query(Q[:m], W.k, 0, ids[:m])
             launch_ms[m] = g.last_timing()["search"]
         g.close()
-        _exp_line(experiment="tail", workload=W.name, storage={0: "fp32", 1: "bf16"}[storage],
-                  n=W.n_init + 2 * W.batch,
+        _exp_line(experiment="tail", workload=W.name, storage={0: "fp32", 1: "bf16"}[storage], batch=B,
+                  n=W.n_init + 2 * B,
                   insert_batch_search_ms=search_ms, per_insert_percentiles_0_50_90_99_100=pct,
                   query_launch_ms=launch_ms)
         del X0, Xs, Q

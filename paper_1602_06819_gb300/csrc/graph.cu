@@ -74,6 +74,7 @@ struct knn_graph {
     int32_t *touched = nullptr;
     int32_t *frontier = nullptr;
     unsigned *small = nullptr;  // [0] offers, [1] touched, [2] error flags
+    unsigned *work = nullptr;   // search counter of the persistent off-chip search
     unsigned long long *totals = nullptr;
     int64_t *out_ids_dev = nullptr;
     float *out_sims_dev = nullptr;
@@ -326,6 +327,7 @@ static knn_status run_search(knn_graph *g, const float *queries, int64_t m, int 
     a.vis_n = (uint32_t)g->n;
     a.speedup = g->p.speedup;
     a.streams = streams;
+    a.work = g->work;
     CU(launch_search(g->p.storage, g->dp, a, s));
     g->last_counters_src = g->counters;
     ++g->launches;
@@ -476,6 +478,7 @@ static knn_status graph_alloc(const knn_params &p, cudaStream_t s, knn_graph **o
     ALLOC(touched, g->offer_cap)
     ALLOC(frontier, M * levels)
     ALLOC(small, 4)
+    ALLOC(work, 4)
     ALLOC(totals, NTOT)
     ALLOC(out_ids_dev, M * K)
     ALLOC(out_sims_dev, M * K)
@@ -1034,6 +1037,7 @@ static knn_status query_partitioned(knn_graph *g, const float *vecs, int64_t m, 
         a.part_live = g->part_live;
         a.speedup = g->p.speedup;
         a.vis_n = (uint32_t)largest;
+        a.work = g->work;
         CU(launch_search(g->p.storage, g->dp, a, s));
         // the k_out (or KT) best of each query's parts * KT candidates
         CU(launch_merge_parts(g->keys_search, (int32_t)mq, parts, KT, g->keys_merge, g->counters,
@@ -1226,6 +1230,7 @@ static knn_status run_search_distributed(knn_graph *g, int64_t n0, int64_t m, cu
         a.part_live = g->part_live;
         a.speedup = g->p.speedup;
         a.vis_n = (uint32_t)largest;
+        a.work = g->work;
         CU(launch_search(g->p.storage, g->dp, a, s));
         CU(launch_part_keys_to_nodes(g->keys_search, mq * P * KT, g->d_order, s));
         CU(launch_merge_parts(g->keys_search, (int32_t)mq, P, KT, g->keys_merge + (size_t)q0 * KT, g->counters,

@@ -94,6 +94,11 @@ struct SearchArgs {
     uint32_t vis_n = 0;                  // bits of one visited set (n, or the largest partition)
     const uint64_t *streams = nullptr;   // nullable: restart stream of query i (replaces stream_base + i)
     Segments seg;                        // several graphs: item i searches graph seg.item_seg[i]
+    // nullable: with visited sets in global memory, the searches are taken one
+    // at a time from this counter (zeroed by the launcher) by a grid of the
+    // warps that fit on the GPU at once, so that a warp that ends early takes
+    // the next search instead of idling until its block ends
+    unsigned *work = nullptr;
 };
 constexpr uint64_t PART_STREAM_STEP = 1ull << 56;
 

@@ -105,8 +105,12 @@ __device__ __forceinline__ void offer_lanes(WarpTop<T> &top, unsigned lanes, uin
     }
 }
 
+// Two blocks a SM with visited sets in shared memory (their size decides);
+// with visited sets in global memory, three (at most 168 registers a
+// thread): the searches of DRAM-resident graphs wait on memory round trips,
+// and more of them in flight finish a batch sooner.
 template <int STORAGE, int DP, int T, bool SMEM_VIS>
-__global__ void __launch_bounds__(SEARCH_WARPS * 32, 8 / SEARCH_WARPS)
+__global__ void __launch_bounds__(SEARCH_WARPS * 32, SMEM_VIS ? 8 / SEARCH_WARPS : 3)
 ignns_search_kernel(const SearchArgs a) {
     using C = RowCfg<STORAGE, DP>;
     constexpr int NB = 32;  // restart candidates per batch (one a lane)
@@ -132,7 +136,15 @@ ignns_search_kernel(const SearchArgs a) {
     // search sw: query sw / parts over partition sw % parts, the nodes
     // lo .. lo + np - 1 (one partition: every node); with several graphs,
     // item sw over its graph's nodes
-    for (int si = blockIdx.x * SEARCH_WARPS + wib; si < nsearch; si += nwarps) {
+    // the next search of this warp: the static stride, or the counter
+    const bool fetch = !SMEM_VIS && a.work != nullptr;
+    auto next_search = [&](int cur) {
+        if (!fetch) return cur + nwarps;
+        int v = 0;
+        if (lane == 0) v = (int)atomicAdd(a.work, 1u);
+        return __shfl_sync(FULL, v, 0);
+    };
+    for (int si = fetch ? next_search(0) : blockIdx.x * SEARCH_WARPS + wib; si < nsearch; si = next_search(si)) {
         // several graphs: the step's tables may give the order the warps take
         // the items in (a search's result does not depend on when it runs)
         const int sw = (multi && a.seg.order) ? a.seg.order[si] : si;
@@ -522,6 +534,19 @@ static cudaError_t launch_search_t(const SearchArgs &a, cudaStream_t s) {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         ignns_search_kernel<ST, DPV, T, true><<<grid, SEARCH_WARPS * 32, smem, s>>>(a);
+    } else if (a.work) {
+        // persistent: as many blocks as fit at once, the searches taken from
+        // the counter
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ignns_search_kernel<ST, DPV, T, false>,
+                                                              SEARCH_WARPS * 32, 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.work, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        const int cap = (per_sm > 0 ? per_sm : 1) * sms;
+        ignns_search_kernel<ST, DPV, T, false><<<grid < cap ? grid : cap, SEARCH_WARPS * 32, 0, s>>>(a);
     } else {
         ignns_search_kernel<ST, DPV, T, false><<<grid, SEARCH_WARPS * 32, 0, s>>>(a);
     }
