@@ -69,7 +69,8 @@ def parse_args():
                          "one JSON line per point")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true",
-                    help="skip the precision record (BF16 / FP8 / FP32 searches at 1,000,000 x 96)")
+                    help="skip the extra records: the precision record (BF16 / FP8 / FP32 searches at "
+                         "1,000,000 x 96), the speedup sweep and the query batches")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
@@ -415,6 +416,65 @@ def recall_record(recall, recall_new, q, n_final, seq):
                                   "bound": 0.01,
                                   "within": abs(d_all) <= 0.01 and abs(d_new) <= 0.01}
     return rec
+
+
+def run_speedup_sweep(knn, torch, cfg, X0, Xs, Wm, K, B, exact, flush):
+    """The configuration's search-budget sweep: the same stream and batches
+    as the headline at speedup 8, 16 and 32 (n / speedup similarities per
+    insert), each on a fresh graph from the same exact initial graph;
+    inserts/s over the K timed batches (L2 flushed between them), the edge
+    recall of all lists and of the inserted lists against the same exact
+    graph, and the similarities per insert."""
+    import dataclasses
+    n0 = X0.shape[0]
+    out = []
+    for speedup in (8.0, 16.0, 32.0):
+        g = knn.Graph(dataclasses.replace(cfg, speedup=speedup), X0)
+        for i in range(Wm):
+            g.insert(Xs[i * B:(i + 1) * B])
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        st0 = g.stats()
+        for i in range(K):
+            flush.fill_(float(i))
+            a, b = ev[i]
+            a.record()
+            g.insert(Xs[(Wm + i) * B:(Wm + i + 1) * B])
+            b.record()
+        torch.cuda.synchronize()
+        st1 = g.stats()
+        n = st1["n"]
+        online = torch.empty((n, exact.shape[1]), dtype=torch.int64, device="cuda")
+        g.edges(online)
+        g.close()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        out.append({"speedup": speedup, "inserts_per_s": K * B / (ms / 1e3), "ms_per_step": ms / K,
+                    "edge_recall": edge_recall(torch, online, exact) / exact.numel(),
+                    "inserted_recall": edge_recall(torch, online[n0:], exact[n0:]) / ((n - n0) * exact.shape[1]),
+                    "search_evals_per_insert": (st1["search_evals"] - st0["search_evals"]) / (K * B)})
+        del online
+    return out
+
+
+def run_query_record(knn, torch, g, W, Xall):
+    """Queries (Sec. 3's search, no update) on the final graph: 1,024-query
+    batches of the workload's query stream, 5 timed after 1, and their
+    recall@k against exhaustive search of the same nodes."""
+    Q = torch.from_numpy(W.queries(1024)).cuda()
+    k = W.k
+    ids = torch.empty((1024, k), dtype=torch.int64, device="cuda")
+    g.query(Q, k, 0, ids)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in ev:
+        a.record()
+        g.query(Q, k, 0, ids)
+        b.record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    truth = torch.cdist(Q, Xall).topk(k, largest=False).indices
+    hit = int((ids[:, :, None] == truth[:, None, :]).any(-1).sum().item())
+    return {"batch": 1024, "queries_per_s": 1024 / (ms / 1e3), "ms_per_batch": ms,
+            "recall_at_k": hit / truth.numel(), "graph_n": Xall.shape[0]}
 
 
 def run_precision_record(knn, torch, np, hbm_peak, peak_src, steps=20, warmup=3):
@@ -1156,7 +1216,9 @@ def main():
     recall = e_c / exact.numel()
     recall_new = e_c_new / ((n_final - W.n_init) * W.k)
     q = quality_q(e_c, W.n_init, n_final - W.n_init, W.k)
-    del exact, online, Xall
+    extras = rank == 0 and world == 1 and args.workload == "plain" and not args.no_precision
+    queries = run_query_record(knn, torch, g, W, Xall) if extras else None
+    del online, Xall
     seq = sequential_oracle_recall(args, W, n_final - W.n_init) if rank == 0 else None
 
     # roofline of the dominant kernel (the iGNNS search)
@@ -1202,8 +1264,10 @@ def main():
                "h2d_bytes_per_step": B * W.mixture.d * 4,
                "d2h_bytes_per_step": B * W.k * 8}
 
+    sweep = run_speedup_sweep(knn, torch, cfg, X0, Xs, Wm, K, B, exact, flush) if extras else None
+    del exact
     precision = None
-    if rank == 0 and world == 1 and args.workload == "plain" and not args.no_precision:
+    if extras:
         del flush
         torch.cuda.empty_cache()
         precision = run_precision_record(knn, torch, np, peak, peak_src)
@@ -1238,6 +1302,8 @@ def main():
                          "algorithmic_bytes_per_launch": alg_bytes_launch,
                          "launch_ms": search_ms},
             "e2e": e2e,
+            "speedup_sweep": sweep,
+            "queries": queries,
             "precision": precision,
             "cpu_baseline": cpu,
             "clocks": clk,
