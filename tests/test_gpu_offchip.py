@@ -92,3 +92,31 @@ def test_offchip_queries_d96_k20(knn, clustered_d96, storage, amb):
     mix, X, ids = clustered_d96
     compare(knn, X, mix.sample(48, 3), 20, 20, 16.0, 5.0, seed=4, storage=storage, o_ids=ids,
             max_ambiguous=amb, label=f"off-chip d96 k20, storage {storage}")
+
+
+def test_offchip_queries_beyond_resident_warps(knn, clustered):
+    """With more searches than warps that fit on the GPU at once (4,096
+    queries; three blocks of four warps on each SM), the persistent grid takes
+    them from a counter, several a warp: ids, similarities and counters equal
+    those of the same queries in launches of 256, where every warp takes one."""
+    import torch
+    from test_gpu_search import make_graph
+    mix, X, ids, _ = clustered
+    m = 4096
+    Q = torch.from_numpy(mix.sample(m, 7)).cuda()
+    g = make_graph(knn, X, K, 64.0, 5.0, 4, nbr_ids=ids, max_batch=m)
+    try:
+        a_ids = torch.empty((m, K), dtype=torch.int64, device="cuda")
+        a_sims = torch.empty((m, K), dtype=torch.float32, device="cuda")
+        a_ctr = np.empty((m, 8), np.int64)
+        g.query(Q, K, 0, a_ids, a_sims)
+        g.counters(a_ctr)
+        b_ids, b_sims = torch.empty_like(a_ids), torch.empty_like(a_sims)
+        b_ctr = np.empty((m, 8), np.int64)
+        for q0 in range(0, m, 256):
+            g.query(Q[q0:q0 + 256], K, q0, b_ids[q0:q0 + 256], b_sims[q0:q0 + 256])
+            g.counters(b_ctr[q0:q0 + 256])
+    finally:
+        g.close()
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_sims, b_sims)
+    assert np.array_equal(a_ctr, b_ctr)
