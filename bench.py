@@ -477,12 +477,13 @@ def run_query_record(knn, torch, g, W, Xall):
             "recall_at_k": hit / truth.numel(), "graph_n": Xall.shape[0]}
 
 
-def run_precision_record(knn, torch, np, hbm_peak, peak_src, steps=20, warmup=3):
+def run_precision_record(knn, torch, np, hbm_peak, peak_src, steps=4, warmup=2):
     """The precision workload (1,000,000 initial points, d = 96, 1,000
     components, k = 20), one graph per searched copy: FP32, BF16 and
     FP8-E4M3 screening with an FP32 re-score of the best 4k candidates.  Per
-    form: insert batches of the workload's size (4,096 points) timed as the
-    main line times them (L2 flushed between steps), the search kernel's
+    form: 4 insert batches of the workload's size (8,192 points) after 2,
+    49,152 inserts in all, timed as the main line times them (L2 flushed
+    between steps), the search kernel's
     roofline, the edge recall of the inserted points' lists against the
     exact graph, and the similarity error against FP64 (numpy, on sampled
     pairs): of the lists' FP32 similarities, and of the screening copy's

@@ -88,11 +88,11 @@ PLAIN_D128 = Workload(
 
 # n = 1,000,000 initial + 1,000,000 inserts, d = 96, 1,000 components,
 # k = 20, screening storage BF16 / FP8-E4M3 with an FP32 re-score of 4k;
-# inserted in batches of 4,096 (the graph is DRAM-resident and a launch lasts
+# inserted in batches of 8,192 (the graph is DRAM-resident and a launch lasts
 # about as long as its slowest search, so larger batches share that time).
 PRECISION_D96 = Workload(
-    name="gmm-d96-n1M+1M-k20-batch4096",
+    name="gmm-d96-n1M+1M-k20-batch8192",
     mixture=Mixture(d=96, components=1000, half_width=20.0, sigma=1.0, seed=31),
-    n_init=1_000_000, n_insert=1_000_000, k=20, batch=4096, speedups=(4, 8, 16, 32))
+    n_init=1_000_000, n_insert=1_000_000, k=20, batch=8192, speedups=(4, 8, 16, 32))
 
 WORKLOADS = {w.name: w for w in (SMALL_D16, PLAIN_D128, PRECISION_D96)}
