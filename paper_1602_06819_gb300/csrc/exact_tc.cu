@@ -18,7 +18,10 @@
 //   warps 4..15 epilogue, three warpgroups: thread r of warpgroup h reads
 //               accumulator lane r (its row), columns 64h .. 64h+63 of each
 //               tile, forms their keys and keeps the 24 smallest it sees.
-// A key below the thread's current 24th is only appended to a per-thread
+// The three lists of a row share a threshold: each publishes its 24th key in
+// shared memory when it changes, and a thread appends only keys below the
+// smallest of the three (published keys only fall, so a stale one is merely
+// looser).  A key below that threshold is only appended to a per-thread
 // buffer in shared memory; when some lane's buffer may not hold 16 more the warp
 // merges all buffers into the sorted lists in lockstep, so the costly
 // insertions of the 32 rows of a warp run together instead of one lane at
@@ -27,7 +30,9 @@
 // The screening is then made exact.  The 72 candidates of a row (24 per
 // warpgroup) are re-scored as FP32 squared differences and the k best kept.
 // Every other column has a screened key at least the smallest of the three
-// lists' last keys; the row is accepted only if a proven bound on the
+// lists' last keys (+inf for a list that never filled): it was either not
+// appended, so at least some list's 24th at that time, or pushed out of its
+// own list; the row is accepted only if a proven bound on the
 // screening error shows that no such column can beat its k-th neighbour,
 // otherwise it is recomputed against every column in FP32 by the CUDA-core
 // kernel.  The lists therefore equal the exact ones up to FP32 rounding of
@@ -75,7 +80,8 @@ template <int NBOX>
 struct TcCfg {
     static constexpr uint32_t A_BYTES = NBOX * TC_UNIT;
     static constexpr uint32_t BUF_BYTES = TC_BUF * TC_EPI * 8;
-    static constexpr uint32_t FIXED = 1024 + A_BYTES + BUF_BYTES + TC_NACC * TC_COLS * 4 + (3 * TC_NACC + 2) * 8 + 16;
+    static constexpr uint32_t FIXED =
+        1024 + A_BYTES + BUF_BYTES + TC_NACC * TC_COLS * 4 + TC_NWG * TC_ROWS * 4 + (3 * TC_NACC + 2) * 8 + 16;
     static constexpr int STAGES = (232448 - FIXED) / (TC_STAGE + 16) < 8 ? (232448 - FIXED) / (TC_STAGE + 16) : 8;
     static constexpr int NBAR = 1 + 2 * STAGES + 3 * TC_NACC + 1;  // a_full, b_full/empty, acc full/empty, yn_full, drain
     static constexpr uint32_t SMEM = FIXED + STAGES * (TC_STAGE + 16);
@@ -142,7 +148,8 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
     uint8_t *Bs = As + Cfg::A_BYTES;                    // S ring stages
     uint64_t *sbuf = (uint64_t *)(Bs + S * TC_STAGE);   // [TC_BUF][TC_EPI] buffered (column, key bits)
     float *s_yn = (float *)(sbuf + TC_BUF * TC_EPI);    // [TC_NACC][TC_COLS] column norms
-    uint64_t *bars = (uint64_t *)(s_yn + TC_NACC * TC_COLS);
+    volatile float *s_thr = s_yn + TC_NACC * TC_COLS;       // [TC_NWG][TC_ROWS] each list's last key
+    uint64_t *bars = (uint64_t *)(s_yn + TC_NACC * TC_COLS + TC_NWG * TC_ROWS);
     uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + S;
     uint64_t *acc_full = bars + 1 + 2 * S, *acc_empty = acc_full + TC_NACC, *yn_full = acc_empty + TC_NACC;
     uint64_t *drain = yn_full + TC_NACC;
@@ -163,6 +170,7 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         mbar_init(drain, 1);
         fence_barrier_init();
     }
+    for (int i = threadIdx.x; i < TC_NWG * TC_ROWS; i += blockDim.x) s_thr[i] = __int_as_float(0x7f800000);
     if (warp == 1) {
         tmem_alloc(tmem_slot, TC_NACC * TC_ACC_STRIDE);
         tmem_relinquish();
@@ -297,7 +305,10 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                 }
             }
             cnt = 0;
+            s_thr[h * TC_ROWS + r] = key[TC_CAND - 1];
             thr = key[TC_CAND - 1];
+#pragma unroll
+            for (int j = 1; j < TC_NWG; ++j) thr = fminf(thr, s_thr[((h + j) % TC_NWG) * TC_ROWS + r]);
         };
         bool ok = true;
         uint32_t c_base = (uint32_t)t0 * TC_COLS;  // first column of tile t0 + t
@@ -309,6 +320,9 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
             if (!ok && lane == 0) atomicOr(err, 16u);
             fence_after_sync();
             if (ok) {
+                // the other lists of this row may have tightened theirs
+#pragma unroll
+                for (int j = 1; j < TC_NWG; ++j) thr = fminf(thr, s_thr[((h + j) % TC_NWG) * TC_ROWS + r]);
                 const uint32_t ta = tmem + lane_base + buf * TC_ACC_STRIDE + TC_WG_COLS * h;
                 const float *yn = s_yn + buf * TC_COLS + TC_WG_COLS * h;
                 const uint32_t col0 = (uint32_t)c_base + TC_WG_COLS * h;
@@ -461,7 +475,7 @@ __global__ void tc_merge_parts_kernel(int64_t n, int64_t row_begin, int parts, c
     }
     if (lane < TC_CAND) {
         cand_id[row * TC_NCAND + h * TC_CAND + lane] = failed ? -1 : my_id;
-        cand_key[row * TC_NCAND + h * TC_CAND + lane] = my_key;
+        cand_key[row * TC_NCAND + h * TC_CAND + lane] = failed ? -INF : my_key;
     }
 }
 
@@ -498,7 +512,6 @@ __global__ void tc_rescore_kernel(const float *X, const float *norm2, const unsi
     const RowSource src{reinterpret_cast<const uint8_t *>(X), nullptr};
     WarpTop<1> top;
     top.init(k);
-    int full = 0;  // warpgroup lists holding TC_CAND candidates
     float thr = __int_as_float(0x7f800000);
 #pragma unroll 1
     for (int h = 0; h < TC_NWG; ++h) {
@@ -507,7 +520,6 @@ __global__ void tc_rescore_kernel(const float *X, const float *norm2, const unsi
         const float d2 = gather_d2<ST_FP32, DP>(src, cid >= 0 ? (uint32_t)cid : 0u, nc, qv);
         for (int i = 0; i < nc; ++i)
             top.offer(pack_key(__shfl_sync(FULL, d2, i), (uint32_t)__shfl_sync(FULL, cid, i)));
-        full += nc == TC_CAND;
         thr = fminf(thr, cand_key[u * TC_NCAND + h * TC_CAND + TC_CAND - 1]);
     }
     if (lane < k) {
@@ -518,8 +530,9 @@ __global__ void tc_rescore_kernel(const float *X, const float *norm2, const unsi
     // Every column outside the candidates has a screened key >= thr, so a
     // true squared distance >= thr + ||x||^2 - E.  The k-th re-scored
     // distance (FP32, relative error below (DP + 2) 2^-24) must lie below.
+    // A list whose screening gave up carries -inf: the row is redone.
     bool exact = false;
-    if (full == TC_NWG) {
+    if (thr > -__int_as_float(0x7f800000)) {
         const float dk = key_d2(top.entry(k - 1));
         const float xn = norm2[u];
         const float E = screening_error(sqrtf(xn), xn, __uint_as_float(*norm_max), dpt);
