@@ -17,7 +17,8 @@
 //   warp 2      copies each tile's column norms beside its accumulator;
 //   warps 4..15 epilogue, three warpgroups: thread r of warpgroup h reads
 //               accumulator lane r (its row), columns 64h .. 64h+63 of each
-//               tile, forms their keys and keeps the 24 smallest it sees.
+//               tile, forms their keys and keeps the 24 smallest it sees
+//               (20 when k <= 10).
 // The three lists of a row share a threshold: each publishes its 24th key in
 // shared memory when it changes, and a thread appends only keys below the
 // smallest of the three (published keys only fall, so a stale one is merely
@@ -27,8 +28,9 @@
 // insertions of the 32 rows of a warp run together instead of one lane at
 // a time.
 //
-// The screening is then made exact.  The 72 candidates of a row (24 per
-// warpgroup) are re-scored as FP32 squared differences and the k best kept.
+// The screening is then made exact.  The 72 (60) candidates of a row (24, or
+// 20, per warpgroup) are re-scored as FP32 squared differences and the k best
+// kept.
 // Every other column has a screened key at least the smallest of the three
 // lists' last keys (+inf for a list that never filled): it was either not
 // appended, so at least some list's 24th at that time, or pushed out of its
@@ -61,7 +63,9 @@ constexpr int TC_NWG = 3;               // epilogue warpgroups, each with its ow
 constexpr int TC_WG_COLS = TC_COLS / TC_NWG;  // columns of a tile per epilogue thread
 constexpr int TC_ACC_STRIDE = TC_COLS <= 128 ? 128 : 256;  // TMEM columns from one accumulator to the next
 constexpr int TC_NACC = 512 / TC_ACC_STRIDE;  // TMEM accumulators: the MMAs run up to TC_NACC - 1 tiles ahead
-constexpr int TC_CAND = TC_NWG == 2 ? 32 : 24;  // candidates kept per row and warpgroup
+constexpr int TC_CAND = TC_NWG == 2 ? 32 : 24;  // candidates kept per row and warpgroup, at most
+constexpr int TC_CAND_SMALL_K = 20;     // the list of a warpgroup when k <= TC_SMALL_K
+constexpr int TC_SMALL_K = 10;
 constexpr int TC_NCAND = TC_NWG * TC_CAND;  // candidates per row
 constexpr int TC_EPI = TC_NWG * 128;    // epilogue threads
 constexpr int TC_THREADS = 128 + TC_EPI;  // 4 warps for the copies, the MMAs and the norms, then the epilogue
@@ -118,9 +122,10 @@ __global__ void tc_split_kernel(const float *X, int64_t n, int64_t n_pad, int dp
 }
 
 // insert (k, v) into the ascending list of the TC_CAND smallest keys
-__device__ __forceinline__ void cand_insert(float (&key)[TC_CAND], int (&id)[TC_CAND], float k, int v) {
+template <int L>
+__device__ __forceinline__ void cand_insert(float (&key)[L], int (&id)[L], float k, int v) {
 #pragma unroll
-    for (int i = TC_CAND - 1; i > 0; --i) {
+    for (int i = L - 1; i > 0; --i) {
         const bool shift = k < key[i - 1];
         const bool here = !shift && k < key[i];
         key[i] = shift ? key[i - 1] : (here ? k : key[i]);
@@ -132,7 +137,9 @@ __device__ __forceinline__ void cand_insert(float (&key)[TC_CAND], int (&id)[TC_
     }
 }
 
-template <int NBOX>
+// L: the length of a warpgroup's candidate list (the rest of its TC_CAND
+// slots are written empty)
+template <int NBOX, int L>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant__ CUtensorMap t_lo,
                 const __grid_constant__ CUtensorMap t_bhi, const __grid_constant__ CUtensorMap t_blo,
@@ -285,10 +292,10 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
         const uint32_t row = (uint32_t)(row0 + r);  // rows and columns are below 2^31
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         uint64_t *mybuf = sbuf + te;  // entry e at mybuf[e * TC_EPI]
-        float key[TC_CAND];
-        int id[TC_CAND];
+        float key[L];
+        int id[L];
 #pragma unroll
-        for (int i = 0; i < TC_CAND; ++i) {
+        for (int i = 0; i < L; ++i) {
             key[i] = __int_as_float(0x7f800000);
             id[i] = -1;
         }
@@ -301,12 +308,12 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
                 if (e < cnt) {
                     const uint2 ent = reinterpret_cast<const uint2 *>(mybuf)[e * TC_EPI];
                     const float kk = __uint_as_float(ent.y);
-                    if (kk < key[TC_CAND - 1] && ent.x != row) cand_insert(key, id, kk, (int)ent.x);
+                    if (kk < key[L - 1] && ent.x != row) cand_insert(key, id, kk, (int)ent.x);
                 }
             }
             cnt = 0;
-            s_thr[h * TC_ROWS + r] = key[TC_CAND - 1];
-            thr = key[TC_CAND - 1];
+            s_thr[h * TC_ROWS + r] = key[L - 1];
+            thr = key[L - 1];
 #pragma unroll
             for (int j = 1; j < TC_NWG; ++j) thr = fminf(thr, s_thr[((h + j) % TC_NWG) * TC_ROWS + r]);
         };
@@ -405,8 +412,9 @@ exact_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant_
             float *ck = (split ? part_key : cand_key) + at + h * TC_CAND;
 #pragma unroll
             for (int i = 0; i < TC_CAND; ++i) {
-                ci[i] = ok ? id[i] : -1;  // no candidates: the FP32 pass takes the row
-                ck[i] = ok ? key[i] : -__int_as_float(0x7f800000);
+                // no candidates (and -inf keys): the FP32 pass takes the row
+                ci[i] = ok && i < L ? id[i < L ? i : 0] : -1;
+                ck[i] = !ok ? -__int_as_float(0x7f800000) : i < L ? key[i < L ? i : 0] : __int_as_float(0x7f800000);
             }
         }
     }
@@ -501,7 +509,7 @@ __device__ __forceinline__ float screening_error(float xnorm, float xn, float ym
 // fail are appended to `redo`.
 template <int DP>
 __global__ void tc_rescore_kernel(const float *X, const float *norm2, const unsigned *norm_max, int64_t n, int k,
-                                  int dpt, const int32_t *cand_id, const float *cand_key, int32_t *out_ids,
+                                  int dpt, int lc, const int32_t *cand_id, const float *cand_key, int32_t *out_ids,
                                   float *out_d2, int32_t *redo, unsigned *redo_count) {
     using C = RowCfg<ST_FP32, DP>;
     const int lane = threadIdx.x & 31;
@@ -520,7 +528,10 @@ __global__ void tc_rescore_kernel(const float *X, const float *norm2, const unsi
         const float d2 = gather_d2<ST_FP32, DP>(src, cid >= 0 ? (uint32_t)cid : 0u, nc, qv);
         for (int i = 0; i < nc; ++i)
             top.offer(pack_key(__shfl_sync(FULL, d2, i), (uint32_t)__shfl_sync(FULL, cid, i)));
-        thr = fminf(thr, cand_key[u * TC_NCAND + h * TC_CAND + TC_CAND - 1]);
+        // a list's lc-th key: the screened keys of the columns left out are
+        // at least the smallest of these (also for merged lists, which hold
+        // every entry of their parts' lists of lc)
+        thr = fminf(thr, cand_key[u * TC_NCAND + h * TC_CAND + lc - 1]);
     }
     if (lane < k) {
         const uint64_t key = top.e[0];
@@ -619,15 +630,15 @@ static uint64_t g_tc_wait_ns = TC_WAIT;
 
 void exact_tc_set_wait(int64_t ns) { g_tc_wait_ns = ns < 0 ? TC_WAIT : (uint64_t)ns; }
 
-template <int NBOX>
+template <int NBOX, int L>
 static cudaError_t tc_screen(const CUtensorMap &th, const CUtensorMap &tl, const CUtensorMap &tbh,
                              const CUtensorMap &tbl, const float *norm2, int64_t n, const TcPlan &plan,
                              int32_t *cid, float *ckey, int32_t *pid, float *pkey, unsigned *err, cudaStream_t s) {
     const size_t smem = TcCfg<NBOX>::SMEM;
     cudaError_t e =
-        cudaFuncSetAttribute(exact_tc_kernel<NBOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(exact_tc_kernel<NBOX, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    exact_tc_kernel<NBOX><<<(unsigned)plan.grid, TC_THREADS, smem, s>>>(
+    exact_tc_kernel<NBOX, L><<<(unsigned)plan.grid, TC_THREADS, smem, s>>>(
         th, tl, tbh, tbl, norm2, n, plan.full_blocks, plan.parts, cid, ckey, pid, pkey, err, g_tc_wait_ns);
     if ((e = cudaGetLastError()) != cudaSuccess || plan.parts < 2) return e;
     const int64_t row_begin = plan.full_blocks * TC_ROWS;
@@ -638,11 +649,11 @@ static cudaError_t tc_screen(const CUtensorMap &th, const CUtensorMap &tl, const
 }
 
 template <int DP>
-static cudaError_t tc_rescore(const ExactArgs &a, int dpt, const float *norm2, unsigned *counters,
+static cudaError_t tc_rescore(const ExactArgs &a, int dpt, int lc, const float *norm2, unsigned *counters,
                               const int32_t *cid, const float *ckey, int32_t *redo, cudaStream_t s) {
     const int64_t threads = a.n * 32;
     tc_rescore_kernel<DP><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        a.X, norm2, counters, a.n, a.k, dpt, cid, ckey, a.out_ids, a.out_d2, redo, counters + 1);
+        a.X, norm2, counters, a.n, a.k, dpt, lc, cid, ckey, a.out_ids, a.out_d2, redo, counters + 1);
     return cudaGetLastError();
 }
 
@@ -680,15 +691,26 @@ cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned 
     if (e != cudaSuccess) return e;
     tc_split_kernel<<<(unsigned)((n_pad * 32 + 255) / 256), 256, 0, s>>>(a.X, a.n, n_pad, dp, dpt, hi, lo,
                                                                           norm2, counters);
-    e = dpt == 64 ? tc_screen<1>(th, tl, tbh, tbl, norm2, a.n, plan, cid, ckey, pid, pkey, counters + 2, s)
-                  : tc_screen<2>(th, tl, tbh, tbl, norm2, a.n, plan, cid, ckey, pid, pkey, counters + 2, s);
+    // shorter lists for small k: fewer appends and cheaper merges, while the
+    // k-th distance still lies well inside the candidates
+    const int lc = a.k <= TC_SMALL_K ? TC_CAND_SMALL_K : TC_CAND;
+    if (dpt == 64)
+        e = lc == TC_CAND ? tc_screen<1, TC_CAND>(th, tl, tbh, tbl, norm2, a.n, plan, cid, ckey, pid, pkey,
+                                                  counters + 2, s)
+                          : tc_screen<1, TC_CAND_SMALL_K>(th, tl, tbh, tbl, norm2, a.n, plan, cid, ckey, pid, pkey,
+                                                          counters + 2, s);
+    else
+        e = lc == TC_CAND ? tc_screen<2, TC_CAND>(th, tl, tbh, tbl, norm2, a.n, plan, cid, ckey, pid, pkey,
+                                                  counters + 2, s)
+                          : tc_screen<2, TC_CAND_SMALL_K>(th, tl, tbh, tbl, norm2, a.n, plan, cid, ckey, pid, pkey,
+                                                          counters + 2, s);
     if (e != cudaSuccess) return e;
     switch (dp) {
-        case 16: e = tc_rescore<16>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
-        case 32: e = tc_rescore<32>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
-        case 64: e = tc_rescore<64>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
-        case 96: e = tc_rescore<96>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
-        case 128: e = tc_rescore<128>(a, dpt, norm2, counters, cid, ckey, redo, s); break;
+        case 16: e = tc_rescore<16>(a, dpt, lc, norm2, counters, cid, ckey, redo, s); break;
+        case 32: e = tc_rescore<32>(a, dpt, lc, norm2, counters, cid, ckey, redo, s); break;
+        case 64: e = tc_rescore<64>(a, dpt, lc, norm2, counters, cid, ckey, redo, s); break;
+        case 96: e = tc_rescore<96>(a, dpt, lc, norm2, counters, cid, ckey, redo, s); break;
+        case 128: e = tc_rescore<128>(a, dpt, lc, norm2, counters, cid, ckey, redo, s); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
