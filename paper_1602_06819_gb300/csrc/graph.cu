@@ -1126,12 +1126,13 @@ KNN_API knn_status knn_graph_set_partitions(knn_graph *g, const int32_t *labels,
     for (int32_t j = 0; j < parts; ++j)
         if (med[(size_t)j] < 0 || med[(size_t)j] >= n)
             return fail(KNN_ERR_INVALID_ARG, "medoid %d = %lld is not a node", j, (long long)med[(size_t)j]);
-    if (!g->d_label) {
-        // the state, sized for the capacity (the graph does not grow while set)
+    {
+        // the state, sized for the capacity (the graph does not grow while
+        // set); what an earlier call failed to allocate is tried again
         const int64_t C = g->p.capacity;
         knn_status st = KNN_OK;
 #define DALLOC(ptr, count) \
-    if (st == KNN_OK) st = dev_alloc(g, &g->ptr, (size_t)(count));
+    if (st == KNN_OK && !g->ptr) st = dev_alloc(g, &g->ptr, (size_t)(count));
         DALLOC(d_label, C)
         DALLOC(d_medoids, KNN_MAX_PARTS)
         DALLOC(d_order, C)
