@@ -199,12 +199,14 @@ static cudaError_t exact_dp(const ExactArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(exact_knn_kernel<DP, KM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (a.n + EX_ROWS - 1) / EX_ROWS;
+    const int64_t rows = a.rows && a.row_hint > 0 && a.row_hint < a.n ? a.row_hint : a.n;
+    const int64_t blocks = (rows + EX_ROWS - 1) / EX_ROWS;
     const unsigned segs = a.col_segments > 1 && a.rows && a.partial ? (unsigned)a.col_segments : 1u;
     exact_knn_kernel<DP, KM><<<dim3((unsigned)blocks, segs), EX_THREADS, smem, s>>>(a);
     if (segs > 1) {
         // listed rows fill the partial buffer's slots only up to its bound
-        const int64_t warps = EXACT_PARTIAL_SLOTS / segs;
+        int64_t warps = EXACT_PARTIAL_SLOTS / segs;
+        if (a.row_hint > 0 && a.row_hint < warps) warps = a.row_hint;
         exact_merge_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(a);
     }
     return cudaGetLastError();

@@ -724,6 +724,7 @@ cudaError_t launch_exact_tc(int dp, const ExactArgs &a, void *scratch, unsigned 
     rest.rows = redo;
     rest.row_count = counters + 1;
     rest.col_segments = exact_col_segments(nredo, a.n, sms);
+    rest.row_hint = nredo;
     rest.partial = partial;
     return launch_exact(dp, rest, s);
 }

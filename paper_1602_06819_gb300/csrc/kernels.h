@@ -177,6 +177,9 @@ struct ExactArgs {
     // exact_partial_slots() row slots at most) and are merged afterwards
     int32_t col_segments = 1;
     uint64_t *partial = nullptr;
+    // with `rows`: > 0, an upper bound of *row_count known on the host, which
+    // sizes the grid (0: n)
+    int64_t row_hint = 0;
 };
 // column segments that let a pass over `rows` listed rows fill the GPU, and
 // the row slots x segments of partial lists that choice can need
