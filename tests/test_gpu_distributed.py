@@ -200,3 +200,34 @@ def test_distributed_errors(knn):
         assert ei.value.status == knn.KNN_ERR_UNSUPPORTED
     finally:
         g.close()
+
+
+def test_distributed_screening_forms(knn):
+    """The staged copy carries the screening rows (and FP8 scales): four
+    partitions, 2,048 points inserted in batches of 128 into 4,000, with FP32
+    rows and with BF16 and FP8-E4M3 screening copies (FP32 re-score of 4k):
+    the screening forms keep the FP32 form's edge recall within 0.01 (BF16)
+    and 0.02 (FP8), and their labels are the FP32 form's (the assignment
+    reads the FP32 rows)."""
+    mix = Mixture(d=16, components=10, half_width=10.0, sigma=1.0, seed=35)
+    n0, na, B, k, parts = 4000, 2048, 128, 10, 4
+    X0, Xs = mix.sample(n0, 1), mix.sample(na, 2)
+    exact, _, _ = oracle.exact_knn(np.vstack([X0, Xs]), k)
+    lab0, med, _ = oracle.kmedoids(X0, parts, imbalance=1.1, chunks=1, iters=2, seed=3)
+    start = oracle.exact_knn(X0, k)[0]
+    recall, labels = {}, {}
+    for storage in (0, 1, 2):
+        g = make_graph(knn, X0, k, 4.0, 5.0, 6, n0 + na, B, 2, storage=storage, nbr_ids=start)
+        try:
+            g.set_partitions(lab0.copy(), med.copy(), 0.0)
+            for b0 in range(0, na, B):
+                g.insert_distributed(cuda_tensor(Xs[b0:b0 + B]))
+            got, _ = edges(g, n0 + na, k)
+            labels[storage], _, _ = partitions(g, n0 + na, parts)
+        finally:
+            g.close()
+        recall[storage] = _recall(got, exact)
+    print(f"distributed build, screening forms: edge recall FP32 {recall[0]:.4f}, BF16 {recall[1]:.4f}, "
+          f"FP8 {recall[2]:.4f}")
+    assert abs(recall[1] - recall[0]) <= 0.01 and abs(recall[2] - recall[0]) <= 0.02
+    assert np.array_equal(labels[1], labels[0]) and np.array_equal(labels[2], labels[0])
