@@ -106,11 +106,16 @@ __device__ __forceinline__ void offer_lanes(WarpTop<T> &top, unsigned lanes, uin
 }
 
 // Two blocks a SM with visited sets in shared memory (their size decides);
-// with visited sets in global memory, three (at most 168 registers a
-// thread): the searches of DRAM-resident graphs wait on memory round trips,
-// and more of them in flight finish a batch sooner.
+// with visited sets in global memory, three where the kernel fits in 168
+// registers a thread without large spills (rows up to 96 dimensions, or 128
+// in a screening copy): the searches of DRAM-resident graphs wait on memory
+// round trips, and more of them in flight finish a batch sooner.
+template <int STORAGE, int DP>
+constexpr int search_min_blocks(bool smem_vis) {
+    return smem_vis ? 8 / SEARCH_WARPS : (DP <= 96 || (STORAGE != ST_FP32 && DP <= 128)) ? 3 : 2;
+}
 template <int STORAGE, int DP, int T, bool SMEM_VIS>
-__global__ void __launch_bounds__(SEARCH_WARPS * 32, SMEM_VIS ? 8 / SEARCH_WARPS : 3)
+__global__ void __launch_bounds__(SEARCH_WARPS * 32, search_min_blocks<STORAGE, DP>(SMEM_VIS))
 ignns_search_kernel(const SearchArgs a) {
     using C = RowCfg<STORAGE, DP>;
     constexpr int NB = 32;  // restart candidates per batch (one a lane)
