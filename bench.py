@@ -105,12 +105,13 @@ def exact_build_report(W, n, ms, info):
     its time, how many rows the FP32 pass took, and the tensor-pipe view.
     Algorithmic FLOPs are 2 n^2 d (one multiply-add per pair and dimension);
     the screening executes 3 BF16 MMA passes over the dimension padded to
-    64 or 128 and the rows padded to 128."""
+    64 or 128, the rows padded to 128-row blocks and the columns to
+    192-column tiles."""
     d = W.mixture.d
     dpt = 64 if d <= 64 else 128
-    n_pad = -(-n // 128) * 128
+    rows_pad, cols_pad = -(-n // 128) * 128, -(-n // 192) * 192
     alg = 2.0 * n * n * d
-    mma = 3 * 2.0 * n_pad * n_pad * dpt
+    mma = 3 * 2.0 * rows_pad * cols_pad * dpt
     peak, src = bf16_peak()
     return {"n": n, "d": d, "k": W.k, "ms": ms, "path": info["path"],
             "rows_redone": info["rows_redone"], "wait_errors": info["wait_errors"],

@@ -1,0 +1,55 @@
+"""Host logic of bench.py that needs no GPU: the graph-quality formula, the
+recall record's comparison with the sequential oracle, the stored oracle
+recall it reads, and the rule that ties the committed ncu traffic to the
+search kernel's source."""
+import argparse
+import math
+
+import bench
+from paper_1602_06819_gb300 import inputs
+
+
+def test_quality_q_is_the_oracle_formula(orc):
+    for e_c, n, n_a, k in [(900_000, 100_000, 25_600, 10), (10_000, 1000, 1000, 10), (0, 50, 7, 3)]:
+        assert math.isclose(bench.quality_q(e_c, n, n_a, k), orc.quality_q(e_c, n, n_a, k), rel_tol=1e-12)
+
+
+def test_recall_record_holds_batches_to_the_oracle_within_0_01():
+    seq = {"edge_recall": 0.86, "inserted_recall": 0.88}
+    ok = bench.recall_record(0.865, 0.889, 0.6, 125_600, seq)
+    assert ok["delta_vs_oracle"]["within"] and not ok["target_met"]
+    far = bench.recall_record(0.865, 0.869, 0.6, 125_600, seq)
+    assert not far["delta_vs_oracle"]["within"]
+    assert "delta_vs_oracle" not in bench.recall_record(0.9, 0.9, 0.7, 10, None)
+
+
+def test_sequential_oracle_recall_reads_the_fixture():
+    args = argparse.Namespace(speedup=4.0, expansion=5.0, depth=2, storage="fp32", order="none")
+    rec = bench.sequential_oracle_recall(args, inputs.PLAIN_D128, 25_600)
+    assert rec is not None and 0.0 < rec["edge_recall"] < 1.0 and 0.0 < rec["inserted_recall"] < 1.0
+    assert bench.sequential_oracle_recall(args, inputs.PLAIN_D128, 12_345) is None
+    other = argparse.Namespace(speedup=8.0, expansion=5.0, depth=2, storage="fp32", order="none")
+    assert bench.sequential_oracle_recall(other, inputs.PLAIN_D128, 25_600) is None
+
+
+def test_traffic_only_for_the_captured_source(monkeypatch):
+    text = open(bench.SEARCH_PROFILE).read()
+    committed = [ln for ln in text.splitlines() if ln.startswith("traffic_bytes_per_launch:")][0]
+    traffic, src = bench.profiled_traffic()
+    if traffic is not None:   # the summary was taken on the current source
+        assert traffic == float(committed.split(":")[1]) and src.startswith("profiles/")
+    monkeypatch.setattr(bench, "search_source_hash", lambda: "0" * 16)
+    assert bench.profiled_traffic() == (None, None)
+
+
+def test_source_hash_ignores_comments_and_spacing(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1602_06819_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "SEARCH_SOURCES", ["a.cuh"])
+    (csrc / "a.cuh").write_text("int x = 1;  // one\n/* block */ int y;\n")
+    h1 = bench.search_source_hash()
+    (csrc / "a.cuh").write_text("int   x = 1;\n\n int y; // another comment\n")
+    assert bench.search_source_hash() == h1
+    (csrc / "a.cuh").write_text("int x = 2; int y;\n")
+    assert bench.search_source_hash() != h1
