@@ -94,6 +94,64 @@ def test_null_handles_are_rejected(knn):
     knn.lib.knn_graph_destroy(None)  # no-op
 
 
+def test_every_handle_entry_point_rejects_a_null_handle(knn):
+    """Each call that takes a graph, server or multi-graph handle refuses a
+    null one with KNN_ERR_INVALID_ARG before touching any other argument
+    (the other pointers here are valid host buffers, never read)."""
+    lib = knn.lib
+    X = np.zeros((4, 16), np.float32)
+    i64 = np.zeros(64, np.int64)
+    i32 = np.zeros(64, np.int32)
+    u64 = np.zeros(64, np.uint64)
+    f32 = np.zeros(64, np.float32)
+    x, a, b, u, f = X.ctypes.data, i64.ctypes.data, i32.ctypes.data, u64.ctypes.data, f32.ctypes.data
+
+    class Lib:  # addresses cast to whatever pointer type a function's argtypes name
+        def __getattr__(self, name):
+            fn = getattr(knn.lib, name)
+
+            def call(*args):
+                types = fn.argtypes or [None] * len(args)
+                conv = [ctypes.cast(ctypes.c_void_p(v), t)
+                        if isinstance(v, int) and t is not None and issubclass(t, ctypes._Pointer) else v
+                        for v, t in zip(args, types)]
+                return fn(*conv)
+            return call
+    lib = Lib()
+    calls = {
+        "knn_graph_query_ids": lambda: lib.knn_graph_query_ids(None, x, 4, 1, u, a, f, None),
+        "knn_graph_query_partitioned": lambda: lib.knn_graph_query_partitioned(
+            None, x, 4, 1, 0, a, 2, a, f, None),
+        "knn_graph_query_partitioned_ids": lambda: lib.knn_graph_query_partitioned_ids(
+            None, x, 4, 1, u, a, 2, a, f, None),
+        "knn_graph_set_partitions": lambda: lib.knn_graph_set_partitions(None, b, a, 2, 0.1, None),
+        "knn_graph_insert_distributed": lambda: lib.knn_graph_insert_distributed(None, x, 4, a, None, None),
+        "knn_graph_get_partitions": lambda: lib.knn_graph_get_partitions(None, b, a, a, None),
+        "knn_graph_last_counters": lambda: lib.knn_graph_last_counters(None, a, 4, None),
+        "knn_graph_set_timing": lambda: lib.knn_graph_set_timing(None, 1),
+        "knn_graph_last_timing": lambda: lib.knn_graph_last_timing(None, f, 4),
+        "knn_graph_stats": lambda: lib.knn_graph_stats(None, a),
+        "knn_graph_reserve": lambda: lib.knn_graph_reserve(None, 1000, 0, None),
+        "knn_server_submit": lambda: lib.knn_server_submit(None, 0, x, 1, u),
+        "knn_server_wait": lambda: lib.knn_server_wait(None, 1, a, f, None),
+        "knn_server_get_stats": lambda: lib.knn_server_get_stats(None, a),
+        "knn_multi_step": lambda: lib.knn_multi_step(None, x, b, b, u, 4, a, f, None),
+        "knn_multi_set_launch": lambda: lib.knn_multi_set_launch(None, 4),
+        "knn_multi_set_order": lambda: lib.knn_multi_set_order(None, 1),
+        "knn_multi_graph_size": lambda: lib.knn_multi_graph_size(None, 0, a, a),
+        "knn_multi_get_edges": lambda: lib.knn_multi_get_edges(None, 0, a, None),
+    }
+    assert set(calls) <= set(declared_functions())
+    for name, call in calls.items():
+        assert call() == knn.KNN_ERR_INVALID_ARG, name
+        assert knn.lib.knn_last_error().decode(), name
+    sh = ctypes.c_void_p()
+    assert knn.lib.knn_server_create(None, None, ctypes.byref(sh)) == knn.KNN_ERR_INVALID_ARG
+    assert sh.value is None
+    knn.lib.knn_server_destroy(None)  # no-op
+    knn.lib.knn_multi_destroy(None)   # no-op
+
+
 def test_exact_graph_rejects_bad_sizes(knn):
     X = np.zeros((5, 8), np.float32)
     ids = np.zeros((5, 4), np.int64)
