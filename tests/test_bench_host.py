@@ -53,3 +53,36 @@ def test_source_hash_ignores_comments_and_spacing(tmp_path, monkeypatch):
     assert bench.search_source_hash() == h1
     (csrc / "a.cuh").write_text("int x = 2; int y;\n")
     assert bench.search_source_hash() != h1
+
+
+def _bench(*args, env=None):
+    import json
+    import os
+    import subprocess
+    import sys
+    e = dict(os.environ, **(env or {}))
+    out = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"), *args],
+                         capture_output=True, text=True, timeout=600, env=e)
+    assert out.returncode == 0, out.stderr[-2000:]
+    return [json.loads(ln) for ln in out.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_reference_arm_prints_one_line_on_the_host():
+    """The reference arm is the oracle on the host cores: one JSON line with
+    the line's metric, the oracle as cpu_baseline and an e2e that moves no
+    bytes; it needs no GPU."""
+    lines = _bench("--impl", "reference", "--workload", "small", "--steps", "2", "--warmup", "3")
+    assert len(lines) == 1
+    ln = lines[0]
+    assert ln["impl"] == "reference" and ln["metric"] == bench.METRIC and ln["unit"] == bench.UNIT
+    assert ln["higher_is_better"] is True and ln["steps"] == 2 and ln["warmup"] == 3
+    assert ln["value"] > 0 and ln["cpu_baseline"]["value"] == ln["value"]
+    assert ln["cpu_baseline"]["kind"] == "oracle" and ln["cpu_baseline"]["cores"] == 1
+    assert ln["e2e"] == {"value": ln["value"], "unit": ln["unit"], "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": 0}
+    assert ln["config"]["workload"] == "gmm-d16-n1k+1k-k10-batch1"
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    assert _bench("--impl", "reference", "--workload", "small", "--steps", "2", "--warmup", "3",
+                  env={"RANK": "1", "WORLD_SIZE": "2"}) == []
