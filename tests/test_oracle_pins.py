@@ -615,6 +615,26 @@ def test_partitioned_search_labels_draw_streams(orc):
     assert sorted(ids.tolist()) == sorted(want) and tot["evals"] == 3
 
 
+def test_partitioned_searches_break_ties_between_parts_to_the_lower_id(orc):
+    """Two nodes at the same point in different partitions are equally similar
+    to q; the merge of the partitions' results keeps the lower id (the order
+    of the exact graph, Sec. 2.1).  1-D points, q = 0, exhaustive searches."""
+    X = np.array([[1.0], [5.0], [1.0], [7.0]], np.float32)
+    nbr, _, _ = orc.exact_knn(X, 2)
+    q = np.array([0.0], np.float32)
+    # contiguous parts {0, 1} and {2, 3}: nodes 0 and 2 tie at distance 1
+    ids, sims, _, margin = orc.partitioned_search(X, nbr, q, 1, [0, 2, 4], 1.0, math.inf, seed=1, stream=0)
+    assert ids.tolist() == [0] and sims[0] == 0.5
+    ids, _, _, _ = orc.partitioned_search(X, nbr, q, 3, [0, 2, 4], 1.0, math.inf, seed=1, stream=0)
+    assert ids.tolist() == [0, 2, 1]
+    # label parts {1, 2} and {0, 3}: the tie is between part 1's node 0 and part 0's node 2
+    labels = np.array([1, 0, 0, 1], np.int32)
+    ids, sims, _, _ = orc.partitioned_search_labels(X, nbr, q, 1, labels, 2, 1.0, math.inf, seed=1, stream=0)
+    assert ids.tolist() == [0] and sims[0] == 0.5
+    ids, _, _, _ = orc.partitioned_search_labels(X, nbr, q, 4, labels, 2, 1.0, math.inf, seed=1, stream=0)
+    assert ids.tolist() == [0, 2, 1, 3]
+
+
 def test_partitioned_search_labels_is_the_contiguous_search_renumbered(orc):
     """Renumbering the nodes partition by partition (id order within each)
     turns the label partitions into contiguous ones: the two searches agree."""
@@ -642,6 +662,11 @@ def test_nearest_medoid_hand_example(orc):
     labels, margins = orc.nearest_medoid(X, [0, 1, 2, 3, 4], [0, 4])
     assert labels.tolist() == [0, 0, 0, 0, 1]
     assert margins[3] == 0.0 and margins[2] > 0.0
+    # the margin is the relative gap of the two best similarities 1 / (1 + L2):
+    # x = 4 is at distances 4 and 6, so (1/5 - 1/7) / (1/5) = 2/7; x = 0 at 0
+    # and 10, so (1 - 1/11) / 1 = 10/11
+    assert margins[2] == pytest.approx(2.0 / 7.0, rel=1e-12)
+    assert margins[0] == pytest.approx(10.0 / 11.0, rel=1e-12)
     labels, margins = orc.nearest_medoid(X, [3], [4, 0])       # medoid order decides the tie
     assert labels.tolist() == [0]
 
