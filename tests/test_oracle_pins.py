@@ -22,6 +22,18 @@ def test_splitmix64_published_outputs(orc):
         assert orc.splitmix64_output(seed, j) == out
 
 
+def test_search_key_from_published_outputs(orc):
+    """The restart key of (seed, stream) is mix(seed XOR mix(stream)), mix(v)
+    being output 0 of the generator started at v.  With the published outputs
+    mix(0) and mix(1234567), two keys follow without computing SplitMix64:
+    key(mix(0) XOR 1234567, 0) = mix(1234567) and key(mix(1234567), 1234567)
+    = mix(0)."""
+    pub = {(int(a), int(b)): int(c) for a, b, c in (ln.split() for ln in read_golden("splitmix64.txt"))}
+    mix0, mix1234567 = pub[(0, 0)], pub[(1234567, 0)]
+    assert orc.search_key(mix0 ^ 1234567, 0) == mix1234567
+    assert orc.search_key(mix1234567, 1234567) == mix0
+
+
 def test_draw_closed_forms(orc):
     rng = np.random.default_rng(0)
     for _ in range(200):
@@ -178,6 +190,21 @@ def test_gnns_spends_the_budget_and_moves_uphill(orc):
             r = orc.search(X, nbr, q, 5, speedup, math.inf, seed=3, stream=i, climb="best")
             assert r.evals == math.floor(400 / speedup) and r.discarded == 0
             assert np.all(np.diff(r.sims) <= 0)
+
+
+def test_expansion_test_keeps_equality(orc):
+    """Sec. 3's expansion test discards a restart whose similarity is below
+    s_max / e; one exactly at the bound is kept.  q = 0, e = 2: the first
+    restart (x = 1) sets s_max = 1/2, so the bound is 1/4, which x = 3 meets
+    exactly (1 / (1 + 3)); x = 3.5 falls below it and x = 2.5 above.  Every
+    list points to its own node, so no restart climbs."""
+    q = np.array([0.0], np.float32)
+    nbr = np.array([[0], [1]], np.int64)
+    for x, discarded in ((3.0, 0), (3.5, 1), (2.5, 0)):
+        X = np.array([[1.0], [x]], np.float32)
+        r = orc.search(X, nbr, q, 2, 1.0, 2.0, seed=0, stream=0, draws=[0, 1])
+        assert (r.evals, r.restarts, r.discarded, r.moves) == (2, 2, discarded, 0), x
+        assert r.ids.tolist() == [0, 1]
 
 
 def test_ignns_exhaustive_special_case(orc):
@@ -407,7 +434,7 @@ def test_e4m3_codes_hand_values(orc):
     for v, c in [(0.0, 0x00), (1.0, 0x38), (-1.75, 0xBE), (448.0, 0x7E), (500.0, 0x7E),
                  (-1e9, 0xFE), (2.0**-9, 0x01), (2.0**-6, 0x08), (2.0**-10, 0x00),
                  (3 * 2.0**-11, 0x01), (1.0625, 0x38), (1.1875, 0x3A),
-                 (0.0625 * 1.0625, 0x18), (464.0 - 1e-3, 0x7E)]:
+                 (0.0625 * 1.0625, 0x18), (464.0 - 1e-3, 0x7E), (470.0, 0x7E), (-479.0, 0xFE)]:
         assert orc.e4m3_code(v) == c, v
     for c in range(256):
         if c & 0x7F == 0x7F:
@@ -459,6 +486,37 @@ def test_kmedoids_hand_trace(orc):
         else:
             new = [orc.kmedoids_medoid(X, np.flatnonzero(labels == m))[0] for m in range(len(med))]
             assert new == [int(v) for v in want]
+
+
+def test_kmedoids_linear_penalty_hand_trace(orc):
+    X = np.array([[0.0], [1.0], [10.0], [3.0]], np.float32)
+    for ln in read_golden("kmedoids_penalty4.txt"):
+        med, imb, want = (p.split() for p in ln.split("|"))
+        labels, _ = orc.kmedoids_assign(X, [int(v) for v in med], float(imb[0]), 1)
+        assert labels.tolist() == [int(v) for v in want]
+
+
+def test_kmedoids_init_draws_distinct_nodes(orc):
+    """p = n: the initial medoids are every node once, whatever the seed."""
+    for seed in range(6):
+        assert sorted(orc.kmedoids_init(5, 5, seed=seed).tolist()) == [0, 1, 2, 3, 4]
+
+
+def test_kmedoids_one_iteration_is_its_steps(orc):
+    """iters = 1 is assign (initial medoids), update, assign: Algorithm 4's
+    loop against its steps, each pinned by the hand traces above."""
+    mix = Mixture(d=4, components=5, half_width=6.0, sigma=1.0, seed=21)
+    X = mix.sample(300, 1)
+    p, imb, chunks, seed = 5, 1.2, 2, 7
+    med = orc.kmedoids_init(300, p, seed=seed)
+    labels, _ = orc.kmedoids_assign(X, med, imb, chunks)
+    med1 = np.array([orc.kmedoids_medoid(X, np.flatnonzero(labels == m))[0]
+                     if np.any(labels == m) else med[m] for m in range(p)], np.int64)
+    labels1, _ = orc.kmedoids_assign(X, med1, imb, chunks)
+    got_labels, got_med, _ = orc.kmedoids(X, p, imb, chunks, 1, seed=seed)
+    assert got_med.tolist() == med1.tolist() and np.array_equal(got_labels, labels1)
+    got_labels0, got_med0, _ = orc.kmedoids(X, p, imb, chunks, 0, seed=seed)
+    assert got_med0.tolist() == med.tolist() and np.array_equal(got_labels0, labels)
 
 
 def test_kmedoids_without_penalty_is_nearest_medoid(orc):
