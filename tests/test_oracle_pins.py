@@ -207,6 +207,55 @@ def test_expansion_test_keeps_equality(orc):
         assert r.ids.tolist() == [0, 1]
 
 
+def test_table1_values_follow_its_formula():
+    """Table 1 (Sec. 3) as printed: e_h = k / 2^d, e_l = k - e_h, and e_s and
+    the speedup k / e_s from e_s = (k - e_h) / (1 + e_h) to the printed two
+    decimals."""
+    for ln in read_golden("table1_eager.txt"):
+        k, d = (int(v) for v in ln.split()[:2])
+        e_h, e_l, e_s, speedup = (float(v) for v in ln.split()[2:])
+        assert e_h == k / 2**d and e_l == k - e_h
+        f = (k - e_h) / (1 + e_h)
+        assert abs(f - e_s) < 0.01 and abs(k / f - speedup) < 0.01
+
+
+def test_eager_climb_spends_table1_evaluations_per_node(orc):
+    """The eager climb moves at the first improving neighbour, so with e_h of
+    a node's k neighbours more similar to q, placed uniformly among the list
+    positions, it computes on average (k + 1) / (e_h + 1) similarities at that
+    node: Table 1's e_s = (k - e_h) / (1 + e_h) before the improving one, plus
+    that one; k at a local maximum (e_h = 0).  The GNNS climb computes all k.
+    Enumerated exactly over every placement: q = 0 on a line, the start node
+    at x = 5 (the only restart), improving neighbours at 1..e_h, the others at
+    6, 7, ...; every neighbour's list holds only the start node."""
+    from itertools import combinations
+    q = np.array([0.0], np.float32)
+    for k, e_h in ((4, 1), (10, 1), (10, 2), (10, 3), (10, 0), (6, 6)):
+        better = [1.0 + i for i in range(e_h)]
+        worse = [6.0 + i for i in range(k - e_h)]
+        total_eager, total_best, count = 0, 0, 0
+        for pos in combinations(range(k), e_h):
+            xs, bi, wi = [], iter(better), iter(worse)
+            for i in range(k):
+                xs.append(next(bi) if i in pos else next(wi))
+            X = np.array([[5.0]] + [[x] for x in xs], np.float32)
+            nbr = np.full((k + 1, k), -1, np.int64)
+            nbr[0] = np.arange(1, k + 1)
+            nbr[1:, 0] = 0
+            r = orc.search(X, nbr, q, 1, 1.0, math.inf, seed=0, stream=0, draws=[0])
+            total_eager += r.evals - 1
+            assert r.moves == (1 if e_h else 0)
+            g = orc.search(X, nbr, q, 1, 1.0, math.inf, seed=0, stream=0, draws=[0], climb="best")
+            total_best += g.evals - 1
+            count += 1
+        if e_h:
+            assert total_eager * (e_h + 1) == (k + 1) * count          # mean (k+1)/(e_h+1)
+            assert math.isclose(total_eager / count - 1, (k - e_h) / (1 + e_h))
+        else:
+            assert total_eager == k * count
+        assert total_best == k * count
+
+
 def test_ignns_exhaustive_special_case(orc):
     """speedup = 1 and no expansion test: every node is evaluated, so iGNNS is
     linear search (Sec. 2.1) and returns the exact k nearest -- with either
