@@ -50,7 +50,11 @@ typedef enum knn_status {
     KNN_ERR_OOM = -2,            /* device memory admission refused            */
     KNN_ERR_CAPACITY = -3,       /* the graph or a batch would exceed its size */
     KNN_ERR_CUDA = -4,           /* a CUDA runtime call failed                 */
-    KNN_ERR_DEVICE_TIMEOUT = -5, /* a bounded device wait gave up              */
+    KNN_ERR_DEVICE_TIMEOUT = -5, /* reserved: no call returns it.  The only
+                                  * device waits are the tensor-core exact
+                                  * build's, bounded; one that gives up is
+                                  * counted in knn_exact_info.wait_errors and
+                                  * its rows are settled on the CUDA cores  */
     KNN_ERR_NOT_FOUND = -6,      /* an id that is not in the graph             */
     KNN_ERR_UNSUPPORTED = -7     /* a size outside the compiled kernels        */
 } knn_status;
