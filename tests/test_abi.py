@@ -181,6 +181,23 @@ def test_binding_raises_with_message(knn):
     assert e.value.status == knn.KNN_ERR_UNSUPPORTED
 
 
+def test_binding_checks_dtypes_and_layout_before_the_call(knn):
+    """Argument marshalling refuses what the C ABI cannot take (the ABI sees
+    only pointers): a wrong element type or a strided view, before any call."""
+    p = _params(knn)
+    with pytest.raises(TypeError):
+        knn.knn_graph_create(p, np.zeros((20, 16), np.float64), stream=0)
+    with pytest.raises(ValueError):
+        knn.knn_graph_create(p, np.zeros((20, 32), np.float32)[:, ::2], stream=0)
+    with pytest.raises(TypeError):
+        knn.knn_graph_restore(p, np.zeros((20, 16), np.float32), np.zeros((20, 10), np.int32), stream=0)
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        knn.knn_graph_create(p, torch.zeros(16, 20).t(), stream=0)
+    with pytest.raises(TypeError):
+        knn.knn_graph_create(p, torch.zeros(20, 16, dtype=torch.float16), stream=0)
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     """The binding has no fallback: without the library, import fails."""
     import importlib
