@@ -100,6 +100,18 @@ def bf16_peak():
         return FALLBACK_BF16_TFLOPS, "fallback"
 
 
+def guarded(name, fn, *args, **kwargs):
+    """An auxiliary record of the line: fn's result, or, if it raised, the
+    error in its place (reported on stderr too), so that the headline line
+    is still printed."""
+    try:
+        return fn(*args, **kwargs)
+    except Exception as e:  # noqa: BLE001 -- any failure of an extra record
+        msg = f"{type(e).__name__}: {e}"
+        print(f"bench.py: {name} record failed: {msg}", file=sys.stderr, flush=True)
+        return {"error": msg}
+
+
 def exact_build_report(W, n, ms, info):
     """The exact graph of n points (tensor-core screening + FP32 settling):
     its time, how many rows the FP32 pass took, and the tensor-pipe view.
@@ -1219,7 +1231,7 @@ def main():
     recall_new = e_c_new / ((n_final - W.n_init) * W.k)
     q = quality_q(e_c, W.n_init, n_final - W.n_init, W.k)
     extras = rank == 0 and world == 1 and args.workload == "plain" and not args.no_precision
-    queries = run_query_record(knn, torch, g, W, Xall) if extras else None
+    queries = guarded("queries", run_query_record, knn, torch, g, W, Xall) if extras else None
     del online, Xall
     seq = sequential_oracle_recall(args, W, n_final - W.n_init) if rank == 0 else None
 
@@ -1266,18 +1278,19 @@ def main():
                "h2d_bytes_per_step": B * W.mixture.d * 4,
                "d2h_bytes_per_step": B * W.k * 8}
 
-    sweep = run_speedup_sweep(knn, torch, cfg, X0, Xs, Wm, K, B, exact, flush) if extras else None
+    sweep = (guarded("speedup_sweep", run_speedup_sweep, knn, torch, cfg, X0, Xs, Wm, K, B, exact, flush)
+             if extras else None)
     del exact
     precision = None
     if extras:
         del flush
         torch.cuda.empty_cache()
-        precision = run_precision_record(knn, torch, np, peak, peak_src)
+        precision = guarded("precision", run_precision_record, knn, torch, np, peak, peak_src)
 
     cpu = None
     n_full_avg = n_before + K * B / 2
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(args, W, n_full_avg)
+        cpu = guarded("cpu_baseline", run_cpu_baseline, args, W, n_full_avg)
 
     if rank == 0:
         srt = sorted(step_ms)

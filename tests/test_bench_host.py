@@ -86,3 +86,14 @@ def test_reference_arm_prints_one_line_on_the_host():
 def test_reference_arm_other_ranks_print_nothing():
     assert _bench("--impl", "reference", "--workload", "small", "--steps", "2", "--warmup", "3",
                   env={"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_extra_records_fail_in_place(capsys):
+    """An auxiliary record that raises leaves its error in the line instead
+    of losing the line."""
+    assert bench.guarded("x", lambda a, b=0: a + b, 2, b=3) == 5
+
+    def boom():
+        raise RuntimeError("out of memory")
+    assert bench.guarded("precision", boom) == {"error": "RuntimeError: out of memory"}
+    assert "precision record failed" in capsys.readouterr().err
