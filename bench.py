@@ -706,7 +706,7 @@ def run_distributed_experiment(knn, torch, np):
     10-component Gaussian mixture), one point inserted at a time, k = 10,
     speedup 4, e = 5, DEPTH 2, 8 balanced k-medoids partitions of the
     initial points:
-    (1) the interval between medoid recomputes (Sec. 8): 4,000 initial
+    (1) the interval between medoid recomputes (Sec. 8.5): 4,000 initial
         points + 4,000 added, medoids recomputed at every 10 % of growth or
         never, 10 repetitions; correct edges e_c of the final graph;
     (2) graph quality (Sec. 8.5's experiment): 8,000 + 16,000, e_c and Q

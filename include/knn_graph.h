@@ -122,7 +122,7 @@ typedef struct knn_graph knn_graph; /* opaque, owned by the library */
 typedef enum knn_climb {
     KNN_CLIMB_EAGER = 0, /* iGNNS: move to the first neighbour, in list order,
                             strictly more similar than the current node      */
-    KNN_CLIMB_BEST = 1   /* GNNS (Sec. 2.3): evaluate every unvisited
+    KNN_CLIMB_BEST = 1   /* GNNS (Sec. 2.2): evaluate every unvisited
                             neighbour, move to the most similar one (ties to
                             the earlier position) if it beats the current node */
 } knn_climb;
@@ -176,7 +176,7 @@ KNN_API knn_status knn_graph_query_batch(knn_graph *g, const float *vecs, int64_
                                          int64_t *out_ids, float *out_sims, void *stream);
 
 /*
- * knn_graph_query_batch with one restart stream per query: query i uses
+ * knn_graph_query_batch (iGNNS, Sec. 3) with one restart stream per query: query i uses
  * stream 2^63 + query_ids[i] (query_ids: [m] uint64, host or device), so a
  * query's result depends only on the graph it sees, its vector and its id --
  * not on the other queries of the call.  Arguments and errors otherwise as
@@ -187,7 +187,7 @@ KNN_API knn_status knn_graph_query_ids(knn_graph *g, const float *vecs, int64_t 
                                        void *stream);
 
 /*
- * Partitioned search (Sec. 6, Algorithm 3): every query is searched
+ * Partitioned search (Sec. 5, Algorithm 3): every query is searched
  * independently in each of `parts` partitions of the graph, then the k_out
  * most similar of the parts * k_out candidates are kept.  Partition j is
  * the node range part_offsets[j] .. part_offsets[j+1] - 1 (int64, host or
@@ -261,7 +261,7 @@ KNN_API knn_status knn_graph_insert_distributed(knn_graph *g, const float *vecs,
                                                 int64_t *out_nbrs, void *stream);
 
 /*
- * The partition state: labels [n] (int32), medoids [parts] (node ids) and
+ * The partition state of Algorithm 5 (Sec. 7): labels [n] (int32), medoids [parts] (node ids) and
  * the number of medoid recomputes so far, each nullable, host or device
  * buffers.  KNN_ERR_INVALID_ARG without knn_graph_set_partitions.
  * Synchronises `stream`.
@@ -278,7 +278,9 @@ KNN_API knn_status knn_graph_remove(knn_graph *g, const int64_t *ids, int64_t m,
                                     void *stream);
 
 /*
- * Copy out the adjacency lists of nodes 0 .. min(n, n_cap)-1.
+ * Copy out the adjacency lists of nodes 0 .. min(n, n_cap)-1: the k-nn graph
+ * the online build maintains (Sec. 1), e.g. to count its correct edges
+ * against an exact graph (Sec. 8.5) or to snapshot it for knn_graph_restore.
  * out_ids: [n_cap, k] int64 (-1 for an empty slot); out_sims (nullable):
  * [n_cap, k] float32.  *n_out (host) receives the number of rows written.
  */
@@ -311,7 +313,8 @@ KNN_API knn_status knn_graph_set_timing(knn_graph *g, int32_t enable);
 KNN_API knn_status knn_graph_last_timing(knn_graph *g, float *out_ms, int32_t n);
 
 /*
- * Change the search parameters of a graph for its later inserts and queries:
+ * Change the search parameters of a graph for its later inserts and queries
+ * (iGNNS, Sec. 3; the GNNS climb it is compared with, Sec. 2.2 and Sec. 8.2):
  * speedup (budget B = max(1, floor(n / speedup))), expansion e (<= 0 or
  * +inf: no expansion test) and climb (knn_climb).  GNNS as the paper
  * compares it with iGNNS is climb = KNN_CLIMB_BEST with expansion = +inf; it
@@ -399,7 +402,7 @@ KNN_API knn_status knn_exact_set_wait_limit(int64_t ns);
 KNN_API knn_status knn_graph_reserve(knn_graph *g, int64_t capacity, int64_t headroom_bytes, void *stream);
 
 /*
- * The query search of knn_graph_query_batch (FP32 rows, no removed nodes)
+ * The query search of knn_graph_query_batch (iGNNS, Sec. 3; FP32 rows, no removed nodes)
  * over a graph held in the caller's own device buffers, without any device
  * allocation.  The paper has no counterpart: this exists for callers that
  * cannot allocate device memory -- a process whose device memory is owned by
@@ -438,7 +441,7 @@ KNN_API knn_status knn_search_noalloc(const float *rows, int64_t n, int32_t dim,
                                       float *out_sims, void *stream);
 
 /*
- * Balanced k-medoids (Sec. 7, Algorithm 4) of n points, for a node ordering
+ * Balanced k-medoids (Sec. 6, Algorithm 4) of n points, for a node ordering
  * that makes clusters contiguous and for the partitions of the partitioned
  * search (Algorithm 3, knn_graph_query_partitioned).
  *

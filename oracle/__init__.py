@@ -16,11 +16,11 @@ Every function cites the passage of the paper it follows:
 * :func:`update`        Update (Algorithm 2).
 * :func:`insert_stream` sequential online build (Algorithm 1).
 * :func:`partitioned_search`, :func:`partitioned_search_labels`  distributed
-  search (Sec. 6, Algorithm 3).
-* :func:`kmedoids` and its steps  balanced k-medoids (Sec. 7, Algorithm 4).
+  search (Sec. 5, Algorithm 3).
+* :func:`kmedoids` and its steps  balanced k-medoids (Sec. 6, Algorithm 4).
 * :func:`nearest_medoid`, :func:`medoid_recompute_sizes`,
   :func:`distributed_insert_stream`  distributed online build (Sec. 7,
-  Algorithm 5; the recompute interval of Sec. 8).
+  Algorithm 5; the recompute interval of Sec. 8.5).
 * :func:`correct_edges`, :func:`quality_q`  graph quality (Sec. 8.5).
 * :func:`quantize_bf16`, :func:`quantize_e4m3`  screening storage codes.
 """
@@ -231,7 +231,7 @@ def search(X, nbr_ids, q, k_out: int, speedup: float, expansion: float,
 
 
 # --------------------------------------------------------------------------
-# balanced k-medoids (Sec. 7, Algorithm 4)
+# balanced k-medoids (Sec. 6, Algorithm 4)
 # --------------------------------------------------------------------------
 
 def kmedoids_init(n: int, p: int, seed: int) -> np.ndarray:
@@ -280,7 +280,7 @@ PART_STREAM_STEP = 1 << 56
 
 def partitioned_search(X, nbr_ids, q, k_out: int, part_offsets, speedup: float, expansion: float,
                        seed: int, stream: int, removed=None, climb: str = "eager"):
-    """Distributed search (Sec. 6, Algorithm 3) with contiguous partitions:
+    """Distributed search (Sec. 5, Algorithm 3) with contiguous partitions:
     partition j (nodes part_offsets[j] .. part_offsets[j+1]-1) is searched on
     its own subgraph -- its rows, its lists with the entries that leave it
     dropped -- with budget max(1, floor(size / speedup)) and restart stream
@@ -325,7 +325,7 @@ def partitioned_search(X, nbr_ids, q, k_out: int, part_offsets, speedup: float, 
 
 def partitioned_search_labels(X, nbr_ids, q, k_out: int, labels, parts: int, speedup: float,
                               expansion: float, seed: int, stream: int, climb: str = "eager"):
-    """Distributed search (Sec. 6, Algorithm 3) over partitions given by a
+    """Distributed search (Sec. 5, Algorithm 3) over partitions given by a
     label per node: partition j, its nodes in id order, is searched on its own
     subgraph -- its rows, its lists with the entries that leave it dropped --
     with budget max(1, floor(size / speedup)) and restart stream
@@ -389,7 +389,7 @@ def nearest_medoid(X, rows, medoids):
 
 
 def medoid_recompute_sizes(n_last: int, n_end: int, interval: float, batch: int = 1):
-    """Graph sizes at which the medoids are recomputed (Sec. 8, "Interval
+    """Graph sizes at which the medoids are recomputed (Sec. 8.5, "Interval
     between recomputing medoids"): growing by `batch` nodes at a time from
     n_last to n_end, after every step that leaves the graph at least
     interval * (its size at the last recompute) nodes larger than then."""

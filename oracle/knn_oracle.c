@@ -18,7 +18,7 @@
  *                         budget of n/speedup similarity computations.
  *   orc_search_climb   -- the same search with a choice of climb: the eager
  *                         rule of iGNNS, or the GNNS rule the paper compares
- *                         against (Sec. 2.3, Sec. 3: every neighbour of the
+ *                         against (Sec. 2.2, Sec. 3: every neighbour of the
  *                         current node is evaluated and the search moves to
  *                         the most similar one).
  *   orc_update         -- Update (Algorithm 2): walk from the found neighbours
@@ -28,7 +28,7 @@
  *   orc_rescore        -- exact re-scoring of screening candidates (the
  *                         reduced-precision storage forms; the paper fixes no
  *                         precision, so the exact form is FP64 here).
- *   orc_kmedoids_*     -- balanced k-medoids (Sec. 7, Algorithm 4): the
+ *   orc_kmedoids_*     -- balanced k-medoids (Sec. 6, Algorithm 4): the
  *                         weighted assign step with the capacity penalty
  *                         w(t, m), the medoid update, and their iteration.
  *   orc_correct_edges  -- correct edges e_c of an online graph (Sec. 8.5).
@@ -768,7 +768,7 @@ void orc_quantize_e4m3(const float *X, int64_t n, int32_t d,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Balanced k-medoids (Sec. 7, Algorithm 4).                                 */
+/* Balanced k-medoids (Sec. 6, Algorithm 4).                                 */
 /*                                                                           */
 /* The paper partitions a graph for its distributed search with a balanced   */
 /* k-medoids clustering: p initial medoids drawn at random; the data spread */

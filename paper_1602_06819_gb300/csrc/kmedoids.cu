@@ -1,4 +1,4 @@
-// kmedoids.cu -- balanced k-medoids (Sec. 7, Algorithm 4) on the device: the
+// kmedoids.cu -- balanced k-medoids (Sec. 6, Algorithm 4) on the device: the
 // node ordering that makes clusters contiguous, and the partitions of the
 // partitioned search (Algorithm 3).
 //

@@ -27,7 +27,7 @@
 //   the same round trip as their visited bits; one ballot then finds the
 //   first unvisited neighbour (in list order) that is strictly more similar,
 //   and every unvisited neighbour up to it is committed.  The GNNS climb the
-//   paper compares against (Sec. 2.3) commits every unvisited neighbour and
+//   paper compares against (Sec. 2.2) commits every unvisited neighbour and
 //   moves to the most similar one (a warp minimum) when it beats the
 //   current node.
 //

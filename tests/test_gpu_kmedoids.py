@@ -1,4 +1,4 @@
-"""Balanced k-medoids (Sec. 7, Algorithm 4) on the GPU against the FP64
+"""Balanced k-medoids (Sec. 6, Algorithm 4) on the GPU against the FP64
 oracle: the initial medoids bit-exact; the assignment of every chunk
 identical up to its first decision whose margin is within FP32 reach (one
 flipped decision changes the later penalties, so the comparison of a chunk

@@ -143,7 +143,7 @@ def test_queries_small_d16(knn, speedup, e):
 @pytest.mark.parametrize("d,speedup,e,amb", [(16, 4.0, math.inf, 3), (16, 20.0, math.inf, 0),
                                              (16, 8.0, 5.0, 1), (128, 4.0, math.inf, 14)])
 def test_queries_gnns_climb(knn, d, speedup, e, amb):
-    """GNNS (Sec. 2.3): every unvisited neighbour evaluated, move to the most
+    """GNNS (Sec. 2.2): every unvisited neighbour evaluated, move to the most
     similar; with and without the expansion test."""
     mix = Mixture(d=d, components=10, half_width=10.0 if d == 16 else 20.0, sigma=1.0, seed=11)
     X0, Q = mix.sample(1000 if d == 16 else 3000, 1), mix.sample(96, 3)
@@ -269,7 +269,7 @@ def test_query_results_do_not_depend_on_the_batch(knn):
 
 
 # ---------------------------------------------------------------------------
-# partitioned search (Sec. 6, Algorithm 3)
+# partitioned search (Sec. 5, Algorithm 3)
 # ---------------------------------------------------------------------------
 
 def oracle_partitioned(X0, o_ids, Q, k_out, offs, speedup, e, seed, qid0, storage=0,

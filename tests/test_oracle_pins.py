@@ -163,7 +163,7 @@ def test_ignns_hand_trace_scan_order(orc):
 
 
 def test_gnns_hand_trace(orc):
-    """GNNS climb (Sec. 2.3, Sec. 3) and the eager climb side by side on a
+    """GNNS climb (Sec. 2.2, Sec. 3) and the eager climb side by side on a
     hand-traced six-point line."""
     X = np.array([[10.0], [3.0], [1.0], [8.0], [9.0], [9.5]], np.float32)
     nbr = np.array([[5, 1], [2, 3], [1, 3], [1, 4], [3, 5], [4, 0]], np.int64)
@@ -520,7 +520,7 @@ def test_e4m3_rowwise_scale(orc):
 
 
 # ---------------------------------------------------------------------------
-# balanced k-medoids (Sec. 7, Algorithm 4)
+# balanced k-medoids (Sec. 6, Algorithm 4)
 # ---------------------------------------------------------------------------
 
 def test_kmedoids_hand_trace(orc):
@@ -614,7 +614,7 @@ def test_kmedoids_iterations(orc):
 
 
 # ---------------------------------------------------------------------------
-# partitioned search (Sec. 6, Algorithm 3)
+# partitioned search (Sec. 5, Algorithm 3)
 # ---------------------------------------------------------------------------
 
 def test_partitioned_search_one_part_is_the_search(orc):
